@@ -1,0 +1,227 @@
+"""Pins for the FP64 oracle (CPU only).
+
+Every check compares the oracle with something other than itself: the
+transform's definition summed directly (brute force on tiny shapes), closed
+forms (single cosine modes, impulses, ramps, a textbook DFT), an independent
+library routine (numpy.fft), and invariants the mathematics fixes (Hermitian
+symmetry of a real field's spectrum, Parseval, the x N round trip, linearity,
+the shift theorem).  A dropped term, a wrong sign, a swapped axis or a
+misplaced k2 range fails at least one of them.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel_l2(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+TINY = [(n0, n1, n2) for n0, n1, n2 in itertools.product((2, 3, 4, 5, 6, 8, 10), (2, 3, 5, 6, 12),
+                                                         (2, 4, 6, 10, 16))
+        if n0 * n1 * n2 <= 8192][::3] + [(6, 10, 16), (8, 8, 8), (15, 12, 10), (16, 16, 16)]
+
+
+@pytest.mark.parametrize("shape", TINY)
+def test_r2c_matches_naive_definition(shape):
+    x = synth.uniform_field(shape, seed=11)
+    X = oracle.r2c3d(x)
+    assert X.shape == shape[:2] + (shape[2] // 2 + 1,)
+    assert rel_l2(X, oracle.r2c3d_naive(x)) < 1e-13
+
+
+@pytest.mark.parametrize("shape", TINY[::2])
+def test_c2r_matches_naive_definition_on_any_input(shape):
+    """The inverse is defined for every complex input, Hermitian or not; the
+    imaginary parts of the k2 = 0 and k2 = n2/2 bins must not matter."""
+    n0, n1, n2 = shape
+    H = n2 // 2 + 1
+    rng = np.random.default_rng(7)
+    Y = rng.standard_normal((n0, n1, H)) + 1j * rng.standard_normal((n0, n1, H))
+    y = oracle.c2r3d(Y, n2)
+    assert rel_l2(y, oracle.c2r3d_naive(Y, n2)) < 1e-13
+
+
+def test_textbook_dft4():
+    rows = np.loadtxt(os.path.join(GOLDEN, "dft4_textbook.txt"))
+    expect = rows[:, 1] + 1j * rows[:, 2]
+    got = oracle.fft1d(np.array([1, 2, 3, 4], dtype=np.complex128), -1)
+    assert np.max(np.abs(got - expect)) < 1e-14
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 12, 30, 49, 64, 96, 160, 210, 512])
+def test_fft1d_matches_numpy(n):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    assert rel_l2(oracle.fft1d(x, -1), np.fft.fft(x)) < 1e-13
+    assert rel_l2(oracle.fft1d(x, +1), n * np.fft.ifft(x)) < 1e-13
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (6, 10, 16), (15, 12, 10), (64, 48, 40), (2, 2, 2)])
+def test_r2c_matches_numpy_rfftn(shape):
+    x = synth.uniform_field(shape, seed=3)
+    assert rel_l2(oracle.r2c3d(x), np.fft.rfftn(x)) < 1e-13
+
+
+def test_batch_matches_separate_calls():
+    x = synth.uniform_field((3, 6, 10, 8), seed=5)
+    Xb = oracle.r2c3d(x)
+    for b in range(3):
+        assert np.array_equal(Xb[b], oracle.r2c3d(x[b]))
+    yb = oracle.c2r3d(Xb, 8)
+    for b in range(3):
+        assert np.array_equal(yb[b], oracle.c2r3d(Xb[b], 8))
+
+
+MODES_32 = [(1, 0, 0), (0, 3, 5), (7, -2, 16), (0, 0, 16), (16, 16, 0), (-5, 11, 9)]
+
+
+@pytest.mark.parametrize("k", MODES_32)
+def test_single_cosine_mode_closed_form(k):
+    """cos(k.x) has spectral weight N/2 at k and N/2 at -k (mod n); only the
+    bins with 0 <= k2 <= n2/2 are stored, so a k2 in (0, n2/2) shows one spike,
+    and a k2 in {0, n2/2} shows both.  A self-conjugate k (k = -k mod n) shows N."""
+    n = 32
+    N = n ** 3
+    x = synth.cosine_mode(n, n, n, *k)
+    X = oracle.r2c3d(x)
+    E = np.zeros_like(X)
+    kp = tuple(v % n for v in k)
+    km = tuple((-v) % n for v in k)
+    for kk in (kp, km):
+        if kk[2] <= n // 2:
+            E[kk] += N / 2
+    assert np.max(np.abs(X - E)) < 1e-12 * N
+
+
+def test_delta_closed_form():
+    n0, n1, n2 = 32, 32, 32
+    x = synth.delta_field(n0, n1, n2, 3, 5, 7)
+    X = oracle.r2c3d(x)
+    k0 = np.arange(n0)[:, None, None]
+    k1 = np.arange(n1)[None, :, None]
+    k2 = np.arange(n2 // 2 + 1)[None, None, :]
+    E = np.exp(-2j * np.pi * (3 * k0 / n0 + 5 * k1 / n1 + 7 * k2 / n2))
+    assert np.max(np.abs(X - E)) < 1e-13
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_ramp_closed_form(axis):
+    """x = j_axis: X = (prod of the other lengths) * sum_j j W^{jk} on the
+    axis' line through k = 0 (closed form n/(W^k - 1) for k != 0,
+    n(n-1)/2 at k = 0) and zero elsewhere.  Pins which axis is which."""
+    shape = (6, 10, 16)
+    n = shape[axis]
+    idx = [None, None, None]
+    idx[axis] = slice(None)
+    x = np.broadcast_to(np.arange(n, dtype=np.float64)[tuple(idx)], shape).copy()
+    X = oracle.r2c3d(x)
+    other = np.prod(shape) // n
+    E = np.zeros_like(X)
+    ks = np.arange(n if axis < 2 else n // 2 + 1)
+    W = np.exp(-2j * np.pi * ks / n)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        line = np.where(ks == 0, n * (n - 1) / 2, n / (W - 1))
+    sel = [0, 0, 0]
+    sel[axis] = slice(None)
+    E[tuple(sel)] = other * line
+    assert np.max(np.abs(X - E)) < 1e-11
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (15, 12, 10), (6, 10, 16)])
+def test_hermitian_planes(shape):
+    n0, n1, n2 = shape
+    X = oracle.r2c3d(synth.uniform_field(shape, seed=9))
+    scale = np.linalg.norm(X)
+    for k2 in (0, n2 // 2):
+        P = X[:, :, k2]
+        mirror = np.conj(P[(-np.arange(n0)) % n0][:, (-np.arange(n1)) % n1])
+        assert np.max(np.abs(P - mirror)) <= 1e-14 * scale
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (15, 12, 10)])
+def test_parseval(shape):
+    x = synth.uniform_field(shape, seed=21)
+    X = oracle.r2c3d(x)
+    N = x.size
+    assert abs(oracle.half_energy(X, shape[2]) / N - np.sum(x * x)) < 1e-12 * np.sum(x * x)
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (15, 12, 10), (2, 2, 2), (64, 48, 40)])
+def test_round_trip_times_N(shape):
+    x = synth.uniform_field(shape, seed=1406 + 1)
+    y = oracle.c2r3d(oracle.r2c3d(x), shape[2])
+    assert np.max(np.abs(y - x.size * x)) < 1e-12 * x.size
+
+
+def test_linearity():
+    shape = (12, 10, 8)
+    a = synth.uniform_field(shape, seed=1)
+    b = synth.uniform_field(shape, seed=2)
+    lhs = oracle.r2c3d(2.5 * a - 0.75 * b)
+    rhs = 2.5 * oracle.r2c3d(a) - 0.75 * oracle.r2c3d(b)
+    assert np.max(np.abs(lhs - rhs)) < 1e-12
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_shift_theorem(axis):
+    shape = (12, 10, 8)
+    x = synth.uniform_field(shape, seed=4)
+    X = oracle.r2c3d(x)
+    Xs = oracle.r2c3d(np.roll(x, 1, axis=axis))
+    n = shape[axis]
+    k = np.arange(X.shape[axis])
+    sh = [1, 1, 1]
+    sh[axis] = -1
+    ph = np.exp(-2j * np.pi * k / n).reshape(sh)
+    assert np.max(np.abs(Xs - X * ph)) < 1e-12
+
+
+def test_c2r_ignores_imag_at_dc_and_nyquist_after_columns():
+    """Adding i*c to a whole k2 = 0 line along n0 and n1 changes the 2D
+    inverse of that plane by an imaginary amount only; the real synthesis
+    drops it, so y is unchanged."""
+    n0, n1, n2 = 6, 10, 8
+    rng = np.random.default_rng(2)
+    Y = rng.standard_normal((n0, n1, n2 // 2 + 1)) + 1j * rng.standard_normal((n0, n1, n2 // 2 + 1))
+    y = oracle.c2r3d(Y, n2)
+    Z = Y.copy()
+    # a purely imaginary field in real space at k2 = 0 is i * (2D DFT of a real plane)
+    plane = rng.standard_normal((n0, n1))
+    Z[:, :, 0] += 1j * np.fft.fft2(plane)
+    Z[:, :, -1] += 1j * np.fft.fft2(rng.standard_normal((n0, n1)))
+    assert np.max(np.abs(oracle.c2r3d(Z, n2) - y)) < 1e-12
+
+
+def test_spot_bins_and_points_match_full_oracle():
+    shape = (24, 20, 16)
+    x32 = synth.uniform_field(shape, seed=8).astype(np.float32)
+    X = oracle.r2c3d(x32.astype(np.float64))
+    ks = [(0, 0, 0), (3, 7, 2), (23, 19, 8), (12, 10, 5)]
+    got = oracle.r2c_bins_f32(x32, ks)
+    assert np.max(np.abs(got - np.array([X[k] for k in ks]))) < 1e-11
+    Y64 = (X / 7.0).astype(np.complex64)
+    y = oracle.c2r3d(Y64.astype(np.complex128), shape[2])
+    js = [(0, 0, 0), (5, 3, 15), (23, 19, 1)]
+    gotp = oracle.c2r_points_c64(Y64, shape[2], js)
+    assert np.max(np.abs(gotp - np.array([y[j] for j in js]))) < 1e-9
+
+
+def test_spectrum_as_oracle():
+    """x = c2r(S) for a Hermitian-consistent S gives r2c(x) = N S exactly (up to
+    FP64 rounding): the spectral_velocity field is such an S."""
+    n0, n1, n2 = 32, 24, 20
+    S = synth.spectral_velocity(n0, n1, n2, seed=1408, components=(0,))[0]
+    x = oracle.c2r3d(S, n2)
+    N = n0 * n1 * n2
+    assert 0.3 < np.sqrt(np.mean(x * x)) < 3.0
+    assert rel_l2(oracle.r2c3d(x), N * S) < 1e-13
