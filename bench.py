@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark of the transpose-free 3D r2c + c2r FFT on GB300.
+
+Workload (one step): forward r2c then inverse c2r of a 512 x 512 x 512 FP32
+spectrum-shaped field (random-phase, divergence-free velocity component,
+E(k) ~ k^4 exp(-2 (k/4)^2) below k = 8, k^-5/3 above, 2/3-truncated; seed
+1408), on the plain FP32 transpose-free path, inputs resident in HBM.
+
+Metric: effective HBM throughput = the two-pass minimum bytes of r2c + c2r,
+2 * (4N + 24M) with N = n^3 reals and M = n*n*(n/2+1) complex values, divided
+by the step time; ms per step alongside.  The same bytes/time is reported for
+the end-to-end call with host buffers (``e2e``) and for the FP64 CPU oracle
+(``cpu_baseline``; ``--impl reference`` times only the oracle).
+
+Multi-GPU: the transform is one volume per GPU (replicas only, no exchange):
+each rank transforms its own field; value = all ranks' bytes / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3D r2c+c2r ms & HBM GB/s vs 8 TB/s; split-BF16 TC vs FP32 at stated rel-L2 error"
+UNIT = "GB/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def two_pass_bytes(n0, n1, n2):
+    N = n0 * n1 * n2
+    M = n0 * n1 * (n2 // 2 + 1)
+    return 2 * (4 * N + 24 * M), N, M
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def workload_config(n, args):
+    return {
+        "workload": f"{n}x{n}x{n} FP32 r2c+c2r, transpose-free, spectrum-shaped velocity component (seed 1408)",
+        "n0": n, "n1": n, "n2": n, "batch": 1,
+        "bytes_per_step": two_pass_bytes(n, n, n)[0],
+        "bytes_definition": "2*(4N+24M): one read + one write per pass of the 2-pass minimum, r2c and c2r",
+        "l2": "inputs larger than L2 (0.54 GB real + 0.54 GB complex per field), no flush",
+        "parallelism": f"replicas x{args.gpus}",
+    }
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1406_5597_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(pass_name, n):
+    """dram bytes per launch of a pass, from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    src = kernel_source_hash()
+    for line in open(p):
+        if line.startswith("#") or not line.strip():
+            continue
+        kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
+        if kv.get("pass") == pass_name and kv.get("n") == str(n) and kv.get("src") == src:
+            return float(kv["bytes_per_launch"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fft3d_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_field(n):
+    """Spectrum-shaped half spectrum S (complex64 numpy) of velocity component 0."""
+    import numpy as np
+
+    import synth
+    S = synth.spectral_velocity(n, n, n, seed=synth.seed_for_config(2), components=(0,))[0]
+    return S.astype(np.complex64)
+
+
+def run_reference(args):
+    """FP64 CPU oracle on the host cores, same workload, metric and unit."""
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    n = args.n
+    S = make_field(n)
+    x = oracle.c2r3d(S.astype(np.complex128), n)  # setup, not timed
+    nbytes, _, _ = two_pass_bytes(n, n, n)
+    cores = oracle.threads()
+    t0 = time.perf_counter()
+    X = oracle.r2c3d(x)
+    oracle.c2r3d(X, n)
+    t_first = time.perf_counter() - t0
+    steps = max(1, min(args.steps, int(150.0 / max(t_first, 1e-3))))
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        X = oracle.r2c3d(x)
+        oracle.c2r3d(X, n)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    value = nbytes / (ms * 1e-3) / 1e9
+    sample = (f"full {n}^3 r2c+c2r in FP64 per step; {steps} timed step(s) after 1 warm-up "
+              f"(steps capped so the run stays within a few minutes)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(n, args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def time_steps(fn, stream, steps):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fft3d", choices=["fft3d", "reference"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1406_5597_gb300 as fft3d
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    fft3d.load()
+    n = args.n
+    nbytes, N, M = two_pass_bytes(n, n, n)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+
+    plan = fft3d.Plan(n, n, n)
+    S = make_field(n)
+    Sd = torch.from_numpy(S).to(dev)
+    x = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    plan.c2r(Sd.data_ptr(), x.data_ptr(), sptr)  # the real field (setup)
+    del Sd
+    X = torch.empty((n, n, n // 2 + 1), dtype=torch.complex64, device=dev)
+    y = torch.empty_like(x)
+
+    def step():
+        plan.r2c(x.data_ptr(), X.data_ptr(), sptr)
+        plan.c2r(X.data_ptr(), y.data_ptr(), sptr)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    fft3d.fft3d_set_profiling(plan.handle, True)
+    ms_total = time_steps(step, stream, args.steps)
+    fft3d.fft3d_set_profiling(plan.handle, False)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    prof = fft3d.fft3d_profile_read(plan.handle)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    ms = ms_total / args.steps
+    value = world * nbytes / (ms * 1e-3) / 1e9
+    launches = args.steps * (fft3d.fft3d_launches_per_call(plan.handle, -1) + fft3d.fft3d_launches_per_call(plan.handle, 1))
+
+    # dominant kernel (pass) and its roofline
+    names = fft3d.pass_names()
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / max(1, prof[dom][1])
+    dom_bytes = fft3d.fft3d_pass_bytes(plan.handle, names.index(dom))
+    peak, peak_kind = measured_peak_hbm()
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_from_profile(dom, n), "kernel": dom, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms}
+    passes = {k: {"avg_ms": v[0] / v[1], "launches": v[1],
+                  "gbs": fft3d.fft3d_pass_bytes(plan.handle, names.index(k)) / (v[0] / v[1] * 1e-3) / 1e9}
+              for k, v in prof.items() if v[1]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(n, args),
+        "frac_of_8tbs": value / world / 8000.0, "frac_of_measured_copy": value / world / peak,
+        "roofline": roofline, "passes": passes, "gpu_launches": launches, "clocks": clocks,
+        "plan": plan.describe(),
+    }
+
+    # comparator: the explicit-transpose variant (+1 pass), and with transpose-back (+2)
+    if not args.no_variants:
+        variants = {}
+        for name, flags in (("explicit_transpose", fft3d.FFT3D_FLAG_EXPLICIT_TRANSPOSE),
+                            ("explicit_transpose_back", fft3d.FFT3D_FLAG_EXPLICIT_TRANSPOSE
+                             | fft3d.FFT3D_FLAG_TRANSPOSE_BACK)):
+            vp = fft3d.Plan(n, n, n, flags=flags)
+
+            def vstep(vp=vp):
+                vp.r2c(x.data_ptr(), X.data_ptr(), sptr)
+                vp.c2r(X.data_ptr(), y.data_ptr(), sptr)
+
+            for _ in range(3):
+                vstep()
+            vms = time_steps(vstep, stream, max(5, args.steps // 2)) / max(5, args.steps // 2)
+            variants[name] = {"ms_per_step": vms, "gbs_effective": nbytes / (vms * 1e-3) / 1e9,
+                              "slowdown_vs_transpose_free": vms / ms}
+            vp.close()
+        line["variants"] = variants
+
+    # end to end through the C ABI with host buffers: H2D of x, r2c, c2r, D2H of y
+    if not args.no_e2e:
+        xh = x.cpu().pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+
+        def estep():
+            x.copy_(xh, non_blocking=True)
+            plan.r2c(x.data_ptr(), X.data_ptr(), sptr)
+            plan.c2r(X.data_ptr(), y.data_ptr(), sptr)
+            yh.copy_(y, non_blocking=True)
+
+        for _ in range(3):
+            estep()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        esteps = max(5, args.steps // 2)
+        ems = time_steps(estep, stream, esteps) / esteps
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        line["e2e"] = {"value": world * nbytes / (ems * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ems,
+                       "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N}
+
+    # FP64 CPU oracle on the host cores (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        xs = x.cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        Xo = oracle.r2c3d(xs)
+        oracle.c2r3d(Xo, n)
+        t_cpu = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": nbytes / t_cpu / 1e9, "unit": UNIT, "cores": oracle.threads(),
+                                "kind": "oracle", "ms_per_step": 1e3 * t_cpu,
+                                "sample": f"one full {n}^3 r2c+c2r of the same field in FP64"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * fft3d — transpose-free 3D real-to-complex FFT and its complex-to-real
+ * inverse for one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Chatterjee, Verma & Chaudhuri, "Transpose-free Fast Fourier
+ * Transform for Turbulence Simulation", arXiv:1406.5597.  Sec. 2 defines the
+ * operation (a real n0 x n1 x n2 array to the complex n0 x n1 x (n2/2+1) half
+ * spectrum and back); Sec. 2.1 gives the steps (a 2D r2c per n0-plane, then a
+ * 1D c2c along n0; the inverse in reverse order); Sec. 2.2 replaces the
+ * transpose of step 2 by transforming the n0 axis where it lies, at its
+ * natural stride.  On one GPU this library never materialises a transposed
+ * copy: the n0 pass reads and writes the spectrum in place at stride
+ * n1*(n2/2+1) complex elements.
+ *
+ * Conventions (the paper names FFTW's transforms, Sec. 3, and fixes neither
+ * sign nor scaling; this library takes FFTW's):
+ *   forward  X[k] = sum_j x[j] exp(-2 pi i (k0 j0/n0 + k1 j1/n1 + k2 j2/n2)),
+ *            0 <= k2 <= n2/2;
+ *   inverse  y[j] = sum_{k2=0}^{n2/2} c_k2 Re(sum_{k0,k1} Y[k] exp(+2 pi i (...))),
+ *            c_k2 = 1 at k2 = 0 and k2 = n2/2, else 2; unnormalised, so
+ *            c2r(r2c(x)) = n0*n1*n2 * x.  The imaginary parts of the k2 = 0
+ *            and k2 = n2/2 bins, after the n0 and n1 passes, are ignored.
+ *
+ * Layouts: real data batch x n0 x n1 x n2 contiguous float; complex data
+ * batch x n0 x n1 x H (H = n2/2+1) contiguous interleaved float pairs
+ * (float2, torch.complex64).  C row-major, n2 fastest, batch outermost.
+ * All data pointers are DEVICE pointers unless a comment says otherwise.
+ *
+ * Ownership: the caller owns every data buffer.  A plan owns only its small
+ * twiddle tables and a device status word (allocated at plan time, freed by
+ * fft3d_destroy).  Large workspace, where a variant needs it, is lent by the
+ * caller through fft3d_set_workspace.
+ *
+ * Streams: every launch goes on the stream passed in (a cudaStream_t given
+ * as void*; NULL means the legacy default stream).  Nothing synchronises
+ * implicitly except fft3d_plan*, fft3d_destroy and fft3d_query_device_status.
+ *
+ * Errors: functions returning int return an fft3d_status.  Argument errors
+ * are found before any launch and leave the output untouched.  The status of
+ * the last failing call on the calling thread is kept for fft3d_last_error.
+ */
+#ifndef FFT3D_H
+#define FFT3D_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fft3d_plan_s* fft3d_handle;
+
+/* Arithmetic forms.  Storage is FP32 in every form. */
+typedef enum {
+    FFT3D_F32 = 0,            /* plain FP32 butterflies on the CUDA cores */
+    FFT3D_F32_TC_BF16X3 = 1,  /* radix-16 stages as tensor-core contractions, split-BF16 (3 products) */
+    FFT3D_F32_TC_F16 = 2      /* radix-16 stages as tensor-core contractions, single-term FP16 */
+} fft3d_dtype;
+
+typedef enum {
+    FFT3D_OK = 0,
+    FFT3D_ERR_INVALID_ARG = 1,      /* NULL/overlapping pointers, bad enum, n < 1, batch < 1 */
+    FFT3D_ERR_UNSUPPORTED_SIZE = 2, /* odd n2, a prime factor other than 2, 3, 5, or too long an axis */
+    FFT3D_ERR_MISALIGNED = 3,       /* a data pointer not 16-byte aligned */
+    FFT3D_ERR_ALLOC = 4,            /* plan-time device allocation failed */
+    FFT3D_ERR_CUDA = 5,             /* a CUDA call or launch failed */
+    FFT3D_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up (see fft3d_query_device_status) */
+    FFT3D_ERR_NO_WORKSPACE = 7      /* the variant needs caller workspace and none was set */
+} fft3d_status;
+
+/* Plan flags for fft3d_plan_variant. */
+#define FFT3D_FLAG_EXPLICIT_TRANSPOSE 0x1 /* comparator: materialise the n0<->n1 transpose (Sec. 2.1, step 2) */
+#define FFT3D_FLAG_TRANSPOSE_BACK 0x2     /* with EXPLICIT_TRANSPOSE: transpose back to n0 x n1 x H */
+#define FFT3D_FLAG_THREE_PASS 0x4         /* force separate n2-row, n1-column and n0-column passes */
+#define FFT3D_FLAG_GENERIC 0x8            /* force the runtime-length kernels (testing) */
+
+/*
+ * Create a plan for batch transforms of size n0 x n1 x n2 (Sec. 2).
+ * Requirements: n0, n1 >= 1, n2 >= 2 and even (H = n2/2+1 presumes it), every
+ * prime factor of n0, n1 and n2/2 in {2, 3, 5}, no axis longer than 4096,
+ * batch >= 1, and a current CUDA device.  Chooses the passes and the kernel
+ * shapes, computes twiddle tables in FP64 on the host, rounds them to FP32 and
+ * copies them to the device.  Blocks.  Returns NULL on error (reason in
+ * fft3d_last_error()).
+ */
+fft3d_handle fft3d_plan(int n0, int n1, int n2, int dtype, int batch);
+
+/* As fft3d_plan, with FFT3D_FLAG_* flags. */
+fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, int flags);
+
+/*
+ * Forward r2c (Sec. 2; steps of Sec. 2.1 with the n0 pass of Sec. 2.2).
+ * in:  batch*n0*n1*n2 floats (device), read only.
+ * out: batch*n0*n1*H float2 (device); must not overlap in.
+ * For FFT3D_FLAG_EXPLICIT_TRANSPOSE plans without TRANSPOSE_BACK the result
+ * is laid out batch x n1 x n0 x H ("axes 0 and 1 flipped", Sec. 2.1).
+ * Both pointers 16-byte aligned.  Asynchronous on stream.
+ */
+int fft3d_r2c(fft3d_handle plan, const float* in, void* out, void* stream);
+
+/*
+ * Inverse c2r (Sec. 2; the forward steps in reverse order, Sec. 2.1).
+ * in:  batch*n0*n1*H float2 (device); CLOBBERED (used as scratch, as FFTW's
+ *      multi-dimensional c2r does).  For EXPLICIT_TRANSPOSE plans without
+ *      TRANSPOSE_BACK it is read in the transposed batch x n1 x n0 x H layout.
+ * out: batch*n0*n1*n2 floats (device); must not overlap in.
+ * Unnormalised.  Asynchronous on stream.
+ */
+int fft3d_c2r(fft3d_handle plan, void* in, float* out, void* stream);
+
+/* Release a plan's device tables.  NULL-safe.  Blocks on the device. */
+void fft3d_destroy(fft3d_handle plan);
+
+/* Status of the last failing call on this thread (FFT3D_OK if none). */
+int fft3d_last_error(void);
+
+/* Static text for a status code. */
+const char* fft3d_error_string(int status);
+
+/*
+ * Synchronise stream, then read and clear the plan's device status word.
+ * Returns FFT3D_OK, FFT3D_ERR_TIMEOUT if a bounded device wait gave up, or
+ * FFT3D_ERR_CUDA.
+ */
+int fft3d_query_device_status(fft3d_handle plan, void* stream);
+
+/* Bytes of caller workspace the plan needs (0 when none). */
+size_t fft3d_workspace_bytes(fft3d_handle plan);
+
+/* Lend the plan a device buffer of at least fft3d_workspace_bytes(plan)
+ * bytes, 256-byte aligned; the caller keeps ownership and must keep it
+ * alive while work using the plan is in flight.  NULL detaches. */
+int fft3d_set_workspace(fft3d_handle plan, void* dev_ptr);
+
+/* Plan description for logs: writes a NUL-terminated text of at most len
+ * bytes (host buffer) naming the passes and kernel shapes. */
+int fft3d_describe(fft3d_handle plan, char* text, int len);
+
+/* Number of kernel launches one fft3d_r2c (dir = -1) or fft3d_c2r (dir = +1)
+ * call issues with this plan. */
+int fft3d_launches_per_call(fft3d_handle plan, int dir);
+
+/*
+ * Per-pass timing (tracing).  While enabled, every kernel launch made by
+ * fft3d_r2c / fft3d_c2r is bracketed by two CUDA events recorded on the
+ * launch stream (not for use under stream capture).
+ */
+int fft3d_set_profiling(fft3d_handle plan, int enable);
+
+/* Wait for the recorded events, then write per-pass totals since the last
+ * read into the HOST arrays ms[i] (milliseconds) and count[i] (launches) for
+ * pass ids i < n, and reset.  Pass ids are listed by fft3d_pass_name. */
+int fft3d_profile_read(fft3d_handle plan, double* ms, int* count, int n);
+
+/* Static name of pass id i ("row_r2c", "col_n1_fwd", "col_n0_fwd",
+ * "col_n0_inv", "col_n1_inv", "row_c2r", "swap01"); NULL past the last id. */
+const char* fft3d_pass_name(int pass);
+
+/* Algorithmic bytes one launch of pass id i moves with this plan: one read
+ * plus one write of the data it transforms (4 bytes per real and 8 per complex
+ * value).  Returns 0 for an unknown id. */
+double fft3d_pass_bytes(fft3d_handle plan, int pass);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFT3D_H */

@@ -1,0 +1,297 @@
+"""Python binding of libfft3d (transpose-free 3D r2c / c2r FFT on one GB300).
+
+Argument marshalling only: every step of a transform runs in the library's
+CUDA kernels.  The C functions keep their names (``fft3d_plan``,
+``fft3d_r2c``, ``fft3d_c2r``, ``fft3d_destroy``, ...); data arguments are
+device addresses (ints) and ``stream`` is a ``cudaStream_t`` address (0 for
+the legacy default stream).  ``rfft3`` / ``irfft3`` wrap them for torch CUDA
+tensors, which only provide the device memory and the stream.
+
+There is no CPU path: if ``libfft3d.so`` is missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfft3d.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "fft3d.h")
+
+FFT3D_F32 = 0
+FFT3D_F32_TC_BF16X3 = 1
+FFT3D_F32_TC_F16 = 2
+
+FFT3D_OK = 0
+FFT3D_ERR_INVALID_ARG = 1
+FFT3D_ERR_UNSUPPORTED_SIZE = 2
+FFT3D_ERR_MISALIGNED = 3
+FFT3D_ERR_ALLOC = 4
+FFT3D_ERR_CUDA = 5
+FFT3D_ERR_TIMEOUT = 6
+FFT3D_ERR_NO_WORKSPACE = 7
+
+FFT3D_FLAG_EXPLICIT_TRANSPOSE = 0x1
+FFT3D_FLAG_TRANSPOSE_BACK = 0x2
+FFT3D_FLAG_THREE_PASS = 0x4
+FFT3D_FLAG_GENERIC = 0x8
+
+_lib = None
+_lock = threading.Lock()
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGS = {
+    "fft3d_plan": ([_I, _I, _I, _I, _I], _P),
+    "fft3d_plan_variant": ([_I, _I, _I, _I, _I, _I], _P),
+    "fft3d_r2c": ([_P, _P, _P, _P], _I),
+    "fft3d_c2r": ([_P, _P, _P, _P], _I),
+    "fft3d_destroy": ([_P], None),
+    "fft3d_last_error": ([], _I),
+    "fft3d_error_string": ([_I], ctypes.c_char_p),
+    "fft3d_query_device_status": ([_P, _P], _I),
+    "fft3d_workspace_bytes": ([_P], ctypes.c_size_t),
+    "fft3d_set_workspace": ([_P, _P], _I),
+    "fft3d_describe": ([_P, ctypes.c_char_p, _I], _I),
+    "fft3d_launches_per_call": ([_P, _I], _I),
+    "fft3d_set_profiling": ([_P, _I], _I),
+    "fft3d_profile_read": ([_P, _P, _P, _I], _I),
+    "fft3d_pass_name": ([_I], ctypes.c_char_p),
+    "fft3d_pass_bytes": ([_P, _I], ctypes.c_double),
+}
+
+
+class Fft3dError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {error_string(status)} (status {status})")
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA library in-tree (see native_build.py)."""
+    from . import native_build
+    return native_build.build(force=force, verbose=verbose)
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/fft3d.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fft3d_[a-z0-9_]+)\s*\(", text)))
+
+
+def load():
+    """Load libfft3d.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1406_5597_gb300.build()")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def _v(x):
+    return None if x is None or x == 0 else ctypes.c_void_p(int(x))
+
+
+# --- the C functions, same names ------------------------------------------------
+
+def fft3d_plan(n0, n1, n2, dtype=FFT3D_F32, batch=1):
+    return load().fft3d_plan(n0, n1, n2, dtype, batch)
+
+
+def fft3d_plan_variant(n0, n1, n2, dtype=FFT3D_F32, batch=1, flags=0):
+    return load().fft3d_plan_variant(n0, n1, n2, dtype, batch, flags)
+
+
+def fft3d_r2c(plan, in_ptr, out_ptr, stream=0):
+    return load().fft3d_r2c(_v(plan), _v(in_ptr), _v(out_ptr), _v(stream))
+
+
+def fft3d_c2r(plan, in_ptr, out_ptr, stream=0):
+    return load().fft3d_c2r(_v(plan), _v(in_ptr), _v(out_ptr), _v(stream))
+
+
+def fft3d_destroy(plan):
+    load().fft3d_destroy(_v(plan))
+
+
+def fft3d_last_error():
+    return load().fft3d_last_error()
+
+
+def fft3d_error_string(status):
+    return load().fft3d_error_string(status).decode()
+
+
+def fft3d_query_device_status(plan, stream=0):
+    return load().fft3d_query_device_status(_v(plan), _v(stream))
+
+
+def fft3d_workspace_bytes(plan):
+    return load().fft3d_workspace_bytes(_v(plan))
+
+
+def fft3d_set_workspace(plan, dev_ptr):
+    return load().fft3d_set_workspace(_v(plan), _v(dev_ptr))
+
+
+def fft3d_describe(plan):
+    buf = ctypes.create_string_buffer(512)
+    st = load().fft3d_describe(_v(plan), buf, 512)
+    if st != FFT3D_OK:
+        raise Fft3dError(st, "fft3d_describe")
+    return buf.value.decode()
+
+
+def fft3d_launches_per_call(plan, direction=-1):
+    return load().fft3d_launches_per_call(_v(plan), direction)
+
+
+def fft3d_set_profiling(plan, enable=True):
+    return load().fft3d_set_profiling(_v(plan), 1 if enable else 0)
+
+
+def fft3d_pass_name(pass_id):
+    r = load().fft3d_pass_name(pass_id)
+    return r.decode() if r else None
+
+
+def pass_names():
+    names = []
+    while True:
+        n = fft3d_pass_name(len(names))
+        if n is None:
+            return names
+        names.append(n)
+
+
+def fft3d_profile_read(plan):
+    """{pass name: (total ms, launches)} since the last read."""
+    names = pass_names()
+    n = len(names)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int * n)()
+    st = load().fft3d_profile_read(_v(plan), ms, cnt, n)
+    if st != FFT3D_OK:
+        raise Fft3dError(st, "fft3d_profile_read")
+    return {names[i]: (ms[i], cnt[i]) for i in range(n)}
+
+
+def fft3d_pass_bytes(plan, pass_id):
+    return load().fft3d_pass_bytes(_v(plan), pass_id)
+
+
+def error_string(status: int) -> str:
+    try:
+        return fft3d_error_string(status)
+    except Exception:
+        return "status %d" % status
+
+
+# --- torch helpers (memory and streams only) -----------------------------------
+
+class Plan:
+    """Owning wrapper of a plan handle (and of the workspace it may need)."""
+
+    def __init__(self, n0, n1, n2, dtype=FFT3D_F32, batch=1, flags=0):
+        h = fft3d_plan_variant(n0, n1, n2, dtype, batch, flags)
+        if not h:
+            raise Fft3dError(fft3d_last_error(), "fft3d_plan")
+        self.handle = h
+        self.shape = (n0, n1, n2)
+        self.batch = batch
+        self.flags = flags
+        self.dtype = dtype
+        self._ws = None
+        nbytes = fft3d_workspace_bytes(h)
+        if nbytes:
+            import torch
+            self._ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            st = fft3d_set_workspace(h, self._ws.data_ptr())
+            if st != FFT3D_OK:
+                raise Fft3dError(st, "fft3d_set_workspace")
+
+    def describe(self):
+        return fft3d_describe(self.handle)
+
+    def r2c(self, in_ptr, out_ptr, stream=0):
+        st = fft3d_r2c(self.handle, in_ptr, out_ptr, stream)
+        if st != FFT3D_OK:
+            raise Fft3dError(st, "fft3d_r2c")
+
+    def c2r(self, in_ptr, out_ptr, stream=0):
+        st = fft3d_c2r(self.handle, in_ptr, out_ptr, stream)
+        if st != FFT3D_OK:
+            raise Fft3dError(st, "fft3d_c2r")
+
+    def close(self):
+        if self.handle:
+            fft3d_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_plan_cache: dict = {}
+
+
+def _cached_plan(shape, batch, dtype, flags):
+    key = (tuple(shape), batch, dtype, flags)
+    p = _plan_cache.get(key)
+    if p is None:
+        p = Plan(*shape, dtype=dtype, batch=batch, flags=flags)
+        _plan_cache[key] = p
+    return p
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def rfft3(x, dtype=FFT3D_F32, flags=0, stream=None):
+    """Forward r2c of a float32 CUDA tensor (..., n0, n1, n2) -> complex64
+    (..., n0, n1, n2/2+1); leading dimensions form the batch."""
+    import torch
+    if not (x.is_cuda and x.dtype == torch.float32):
+        raise TypeError("rfft3 needs a float32 CUDA tensor")
+    x = x.contiguous()
+    n0, n1, n2 = x.shape[-3:]
+    batch = int(x.numel() // (n0 * n1 * n2)) if x.numel() else 0
+    out = torch.empty(x.shape[:-1] + (n2 // 2 + 1,), dtype=torch.complex64, device=x.device)
+    if batch == 0:
+        return out
+    _cached_plan((n0, n1, n2), batch, dtype, flags).r2c(x.data_ptr(), out.data_ptr(), _stream_ptr(stream))
+    return out
+
+
+def irfft3(X, n2, dtype=FFT3D_F32, flags=0, inplace_ok=False, stream=None):
+    """Inverse c2r (unnormalised) of a complex64 CUDA tensor (..., n0, n1, n2/2+1).
+    The library clobbers its input, so X is cloned unless inplace_ok."""
+    import torch
+    if not (X.is_cuda and X.dtype == torch.complex64):
+        raise TypeError("irfft3 needs a complex64 CUDA tensor")
+    n0, n1, H = X.shape[-3:]
+    if H != n2 // 2 + 1:
+        raise ValueError("last dimension must be n2/2+1")
+    X = X.contiguous() if inplace_ok else X.clone(memory_format=torch.contiguous_format)
+    batch = int(X.numel() // (n0 * n1 * H)) if X.numel() else 0
+    out = torch.empty(X.shape[:-1] + (n2,), dtype=torch.float32, device=X.device)
+    if batch == 0:
+        return out
+    _cached_plan((n0, n1, n2), batch, dtype, flags).c2r(X.data_ptr(), out.data_ptr(), _stream_ptr(stream))
+    return out

@@ -1,0 +1,522 @@
+// Host side of libfft3d: plan construction (size checks, pass selection,
+// FP64 twiddle tables), the C ABI declared in include/fft3d.h, and the pass
+// sequences of the forward and inverse transforms.
+//
+// Forward (Sec. 2.1 steps 1 and 3, with the n0 step done in place at its
+// natural stride as Sec. 2.2 proposes):
+//   1. n2 rows:   real rows -> half-spectrum rows          (in  -> out)
+//   2. n1 axis:   c2c at stride H per (j0, k2)             (out, in place)
+//   3. n0 axis:   c2c at stride n1*H per flat (k1, k2)     (out, in place)
+// Inverse: the same steps in reverse order (Sec. 2.1), on the clobbered input.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "args.h"
+#include "fft3d.h"
+
+namespace fft3d {
+const LenEntry* entries_small(int* n);
+const LenEntry* entries_mixed(int* n);
+const LenEntry* entries_256_512(int* n);
+const LenEntry* entries_1024_2048(int* n);
+cudaError_t launch_swap01(const float2* in, float2* out, long long batch, long long n0, long long n1, long long H,
+                          cudaStream_t s);
+
+const LenEntry* find_len(int L)
+{
+    using Fn = const LenEntry* (*)(int*);
+    static const Fn groups[] = {entries_small, entries_mixed, entries_256_512, entries_1024_2048};
+    for (Fn f : groups) {
+        int n = 0;
+        const LenEntry* e = f(&n);
+        for (int i = 0; i < n; ++i)
+            if (e[i].L == L) return &e[i];
+    }
+    return nullptr;
+}
+}  // namespace fft3d
+
+using namespace fft3d;
+
+namespace {
+
+constexpr int kMaxAxis = 4096;
+thread_local int g_last_error = FFT3D_OK;
+
+int fail(int status)
+{
+    g_last_error = status;
+    return status;
+}
+
+bool smooth235(long long n)
+{
+    if (n < 1) return false;
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+// exp(+2 pi i m / L) in FP64 with exact quarter-turn reduction:
+// 2 pi m / L = (pi/2) (q + r/L), q = floor(4m/L); the residual angle is taken
+// from the nearer end of [0, pi/2] so that the argument passed to cos/sin is
+// at most pi/4.  Quarter-turn points come out exactly (0, +-1).
+void root_of_unity(long long m, long long L, double* c, double* s)
+{
+    m %= L;
+    if (m < 0) m += L;
+    const long long q = (4 * m) / L;
+    const long long r = 4 * m - q * L;  // in [0, L)
+    const double half_pi = 1.57079632679489661923;
+    double c0, s0;
+    if (2 * r <= L) {
+        const double a = half_pi * (double)r / (double)L;
+        c0 = std::cos(a);
+        s0 = std::sin(a);
+    } else {
+        const double a = half_pi * (double)(L - r) / (double)L;
+        c0 = std::sin(a);
+        s0 = std::cos(a);
+    }
+    switch (q & 3) {
+    case 0: *c = c0; *s = s0; break;
+    case 1: *c = -s0; *s = c0; break;
+    case 2: *c = -c0; *s = -s0; break;
+    default: *c = s0; *s = -c0; break;
+    }
+}
+
+// Forward-sign table W_L^m = exp(-2 pi i m / L), m in [0, count), rounded to FP32.
+std::vector<float2> forward_table(long long L, long long count)
+{
+    std::vector<float2> t((size_t)count);
+    for (long long m = 0; m < count; ++m) {
+        double c, s;
+        root_of_unity(m, L, &c, &s);
+        t[(size_t)m] = make_float2((float)c, (float)(-s));
+    }
+    return t;
+}
+
+GenPlan generic_radices(int L)
+{
+    GenPlan g{};
+    g.L = L;
+    int rem = L;
+    while (rem > 1) {
+        int R = 0;
+        for (int cand : {8, 4, 2, 3, 5})
+            if (rem % cand == 0) { R = cand; break; }
+        g.radix[g.nst++] = R;
+        rem /= R;
+    }
+    return g;
+}
+
+struct Axis {
+    int L = 1;
+    const LenEntry* spec = nullptr;
+    GenPlan gen{};
+    float2* d_tw = nullptr;
+};
+
+}  // namespace
+
+enum PassId { PASS_ROW_R2C = 0, PASS_N1_FWD, PASS_N0_FWD, PASS_N0_INV, PASS_N1_INV, PASS_ROW_C2R, PASS_SWAP01,
+              PASS_COUNT };
+const char* const kPassNames[PASS_COUNT] = {"row_r2c", "col_n1_fwd", "col_n0_fwd", "col_n0_inv",
+                                            "col_n1_inv", "row_c2r", "swap01"};
+
+struct ProfRecord {
+    int pass;
+    cudaEvent_t a, b;
+};
+
+struct fft3d_plan_s {
+    int n0 = 0, n1 = 0, n2 = 0, H = 0, batch = 0, dtype = 0, flags = 0;
+    long long N = 0, M = 0, P = 0;
+    int device = 0;
+    Axis ax0, ax1, ax2;  // ax2: length n2/2 (row transform)
+    float2* d_twpack = nullptr;
+    int* d_status = nullptr;
+    void* workspace = nullptr;
+    std::string desc;
+    bool profiling = false;
+    std::vector<ProfRecord> prof;  // event pairs, reused across reads
+    size_t prof_used = 0;
+};
+
+namespace {
+
+cudaError_t upload(const std::vector<float2>& h, float2** d)
+{
+    cudaError_t e = cudaMalloc((void**)d, h.size() * sizeof(float2));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*d, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice);
+}
+
+void free_plan(fft3d_plan_s* p)
+{
+    if (!p) return;
+    for (ProfRecord& r : p->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    cudaFree(p->ax0.d_tw);
+    cudaFree(p->ax1.d_tw);
+    cudaFree(p->ax2.d_tw);
+    cudaFree(p->d_twpack);
+    cudaFree(p->d_status);
+    delete p;
+}
+
+// Brackets one launch with events when the plan is profiling.
+struct ProfScope {
+    fft3d_plan_s* p;
+    ProfRecord* r = nullptr;
+    cudaStream_t s;
+    ProfScope(fft3d_plan_s* plan, int pass, cudaStream_t stream) : p(plan), s(stream)
+    {
+        if (!p->profiling) return;
+        if (p->prof_used == p->prof.size()) {
+            ProfRecord nr{pass, nullptr, nullptr};
+            if (cudaEventCreate(&nr.a) != cudaSuccess || cudaEventCreate(&nr.b) != cudaSuccess) return;
+            p->prof.push_back(nr);
+        }
+        r = &p->prof[p->prof_used++];
+        r->pass = pass;
+        cudaEventRecord(r->a, s);
+    }
+    ~ProfScope()
+    {
+        if (r) cudaEventRecord(r->b, s);
+    }
+};
+
+bool uses_generic(const fft3d_plan_s* p, const Axis& a, bool row)
+{
+    if (p->flags & FFT3D_FLAG_GENERIC) return true;
+    if (!a.spec) return true;
+    return row ? (a.spec->r2c == nullptr) : false;
+}
+
+cudaError_t run_col(fft3d_plan_s* p, const Axis& a, int dir, float2* data, long long S, long long C,
+                    long long nb, long long Bs, cudaStream_t s)
+{
+    if (a.L <= 1) return cudaSuccess;
+    const bool n0axis = (&a == &p->ax0);
+    ProfScope ps(p, n0axis ? (dir < 0 ? PASS_N0_FWD : PASS_N0_INV) : (dir < 0 ? PASS_N1_FWD : PASS_N1_INV), s);
+    ColArgs ca{data, S, C, nb, Bs, a.d_tw, 1.0f};
+    if (uses_generic(p, a, false)) return generic_col(ca, a.gen, dir, s);
+    return dir < 0 ? a.spec->col_fwd(ca, s) : a.spec->col_inv(ca, s);
+}
+
+cudaError_t run_row(fft3d_plan_s* p, int dir, const void* in, void* out, cudaStream_t s)
+{
+    ProfScope ps(p, dir < 0 ? PASS_ROW_R2C : PASS_ROW_C2R, s);
+    RowArgs ra{in, out, (long long)p->batch * p->n0 * p->n1, p->ax2.d_tw, p->d_twpack};
+    if (uses_generic(p, p->ax2, true)) return generic_row(ra, p->ax2.gen, dir, s);
+    return dir < 0 ? p->ax2.spec->r2c(ra, s) : p->ax2.spec->c2r(ra, s);
+}
+
+std::string axis_desc(const fft3d_plan_s* p, const Axis& a, bool row)
+{
+    char b[96];
+    if (a.L <= 1) return "skip";
+    if (uses_generic(p, a, row)) {
+        std::snprintf(b, sizeof b, "generic L=%d", a.L);
+    } else if (row) {
+        std::snprintf(b, sizeof b, "L=%d E=%d rows/CTA=%d", a.L, a.spec->row_E, a.spec->row_rows);
+    } else {
+        std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d", a.L, a.spec->col_E, a.spec->col_W);
+    }
+    return b;
+}
+
+cudaError_t run_swap(fft3d_plan_s* p, const float2* in, float2* out, long long a0, long long a1, cudaStream_t s)
+{
+    ProfScope ps(p, PASS_SWAP01, s);
+    return launch_swap01(in, out, p->batch, a0, a1, p->H, s);
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fft3d_error_string(int status)
+{
+    switch (status) {
+    case FFT3D_OK: return "ok";
+    case FFT3D_ERR_INVALID_ARG: return "invalid argument";
+    case FFT3D_ERR_UNSUPPORTED_SIZE: return "unsupported size (n2 must be even; n0, n1, n2/2 must be 2,3,5-smooth and <= 4096)";
+    case FFT3D_ERR_MISALIGNED: return "data pointer not 16-byte aligned";
+    case FFT3D_ERR_ALLOC: return "device allocation failed";
+    case FFT3D_ERR_CUDA: return "CUDA error";
+    case FFT3D_ERR_TIMEOUT: return "device-side wait timed out";
+    case FFT3D_ERR_NO_WORKSPACE: return "plan needs caller workspace (fft3d_set_workspace)";
+    default: return "unknown status";
+    }
+}
+
+int fft3d_last_error(void) { return g_last_error; }
+
+fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, int flags)
+{
+    if (n0 < 1 || n1 < 1 || n2 < 2 || batch < 1 || dtype < 0 || dtype > 2 ||
+        (flags & ~(FFT3D_FLAG_EXPLICIT_TRANSPOSE | FFT3D_FLAG_TRANSPOSE_BACK | FFT3D_FLAG_THREE_PASS |
+                   FFT3D_FLAG_GENERIC)) ||
+        ((flags & FFT3D_FLAG_TRANSPOSE_BACK) && !(flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE))) {
+        fail(FFT3D_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    if ((n2 & 1) || !smooth235(n0) || !smooth235(n1) || !smooth235(n2 / 2) || n0 > kMaxAxis || n1 > kMaxAxis ||
+        n2 / 2 > kMaxAxis) {
+        fail(FFT3D_ERR_UNSUPPORTED_SIZE);
+        return nullptr;
+    }
+    if (dtype != FFT3D_F32) {  // tensor-core forms are planned separately
+        fail(FFT3D_ERR_UNSUPPORTED_SIZE);
+        return nullptr;
+    }
+    fft3d_plan_s* p = new (std::nothrow) fft3d_plan_s();
+    if (!p) {
+        fail(FFT3D_ERR_ALLOC);
+        return nullptr;
+    }
+    p->n0 = n0;
+    p->n1 = n1;
+    p->n2 = n2;
+    p->H = n2 / 2 + 1;
+    p->batch = batch;
+    p->dtype = dtype;
+    p->flags = flags;
+    p->N = (long long)n0 * n1 * n2;
+    p->P = (long long)n1 * p->H;
+    p->M = (long long)n0 * p->P;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        fail(FFT3D_ERR_CUDA);
+        return nullptr;
+    }
+    Axis* axes[3] = {&p->ax0, &p->ax1, &p->ax2};
+    const int lens[3] = {n0, n1, n2 / 2};
+    for (int i = 0; i < 3; ++i) {
+        Axis& a = *axes[i];
+        a.L = lens[i];
+        a.spec = find_len(a.L);
+        a.gen = generic_radices(a.L);
+        if (a.L >= 1) {
+            if (upload(forward_table(a.L, a.L), &a.d_tw) != cudaSuccess) {
+                free_plan(p);
+                fail(FFT3D_ERR_ALLOC);
+                return nullptr;
+            }
+        }
+    }
+    if (upload(forward_table(n2, n2 / 2 + 1), &p->d_twpack) != cudaSuccess ||
+        cudaMalloc((void**)&p->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) {
+        free_plan(p);
+        fail(FFT3D_ERR_ALLOC);
+        return nullptr;
+    }
+    std::string d = "rows[" + axis_desc(p, p->ax2, true) + "] n1[" + axis_desc(p, p->ax1, false) + "] n0[" +
+                    axis_desc(p, p->ax0, false) + "]";
+    if (flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE)
+        d += (flags & FFT3D_FLAG_TRANSPOSE_BACK) ? " explicit-transpose+back" : " explicit-transpose";
+    p->desc = d;
+    return p;
+}
+
+fft3d_handle fft3d_plan(int n0, int n1, int n2, int dtype, int batch)
+{
+    return fft3d_plan_variant(n0, n1, n2, dtype, batch, 0);
+}
+
+void fft3d_destroy(fft3d_handle p)
+{
+    if (!p) return;
+    cudaDeviceSynchronize();
+    free_plan(p);
+}
+
+size_t fft3d_workspace_bytes(fft3d_handle p)
+{
+    if (!p) return 0;
+    if (p->flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE) return (size_t)p->batch * (size_t)p->M * sizeof(float2);
+    return 0;
+}
+
+int fft3d_set_workspace(fft3d_handle p, void* dev_ptr)
+{
+    if (!p) return fail(FFT3D_ERR_INVALID_ARG);
+    if (dev_ptr && ((uintptr_t)dev_ptr & 255)) return fail(FFT3D_ERR_MISALIGNED);
+    p->workspace = dev_ptr;
+    return FFT3D_OK;
+}
+
+int fft3d_describe(fft3d_handle p, char* text, int len)
+{
+    if (!p || !text || len < 1) return fail(FFT3D_ERR_INVALID_ARG);
+    std::snprintf(text, (size_t)len, "%dx%dx%d batch=%d %s", p->n0, p->n1, p->n2, p->batch, p->desc.c_str());
+    return FFT3D_OK;
+}
+
+int fft3d_launches_per_call(fft3d_handle p, int dir)
+{
+    if (!p) return fail(FFT3D_ERR_INVALID_ARG);
+    (void)dir;
+    int n = 1 + (p->n1 > 1) + (p->n0 > 1);
+    if (p->flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE) n += (p->flags & FFT3D_FLAG_TRANSPOSE_BACK) ? 2 : 1;
+    return n;
+}
+
+int fft3d_query_device_status(fft3d_handle p, void* stream)
+{
+    if (!p) return fail(FFT3D_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+    if (cudaMemcpy(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess)
+        return fail(FFT3D_ERR_CUDA);
+    return h == 0 ? FFT3D_OK : fail(FFT3D_ERR_TIMEOUT);
+}
+
+int fft3d_r2c(fft3d_handle p, const float* in, void* out, void* stream)
+{
+    if (!p || !in || !out) return fail(FFT3D_ERR_INVALID_ARG);
+    if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return fail(FFT3D_ERR_MISALIGNED);
+    const size_t in_bytes = (size_t)p->batch * p->N * sizeof(float);
+    const size_t out_bytes = (size_t)p->batch * p->M * sizeof(float2);
+    if (overlaps(in, in_bytes, out, out_bytes)) return fail(FFT3D_ERR_INVALID_ARG);
+    const bool xpose = p->flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE;
+    if (xpose && !p->workspace) return fail(FFT3D_ERR_NO_WORKSPACE);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long H = p->H, n0 = p->n0, n1 = p->n1, B = p->batch;
+    float2* o = (float2*)out;
+    cudaError_t e;
+    if (!xpose) {
+        if ((e = run_row(p, -1, in, o, s)) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if ((e = run_col(p, p->ax1, -1, o, H, H, B * n0, n1 * H, s)) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if ((e = run_col(p, p->ax0, -1, o, p->P, p->P, B, p->M, s)) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        return FFT3D_OK;
+    }
+    float2* w = (float2*)p->workspace;
+    if (!(p->flags & FFT3D_FLAG_TRANSPOSE_BACK)) {
+        // plane passes into the workspace, transpose into out, n0 pass on out
+        // (now the middle axis: element (k1, j0, k2) at (k1*n0 + j0)*H + k2)
+        if (run_row(p, -1, in, w, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_col(p, p->ax1, -1, w, H, H, B * n0, n1 * H, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_swap(p, w, o, n0, n1, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_col(p, p->ax0, -1, o, H, H, B * n1, n0 * H, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+    } else {
+        if (run_row(p, -1, in, o, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_col(p, p->ax1, -1, o, H, H, B * n0, n1 * H, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_swap(p, o, w, n0, n1, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_col(p, p->ax0, -1, w, H, H, B * n1, n0 * H, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_swap(p, w, o, n1, n0, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+    }
+    return FFT3D_OK;
+}
+
+int fft3d_c2r(fft3d_handle p, void* in, float* out, void* stream)
+{
+    if (!p || !in || !out) return fail(FFT3D_ERR_INVALID_ARG);
+    if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return fail(FFT3D_ERR_MISALIGNED);
+    const size_t in_bytes = (size_t)p->batch * p->M * sizeof(float2);
+    const size_t out_bytes = (size_t)p->batch * p->N * sizeof(float);
+    if (overlaps(in, in_bytes, out, out_bytes)) return fail(FFT3D_ERR_INVALID_ARG);
+    const bool xpose = p->flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE;
+    if (xpose && !p->workspace) return fail(FFT3D_ERR_NO_WORKSPACE);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long H = p->H, n0 = p->n0, n1 = p->n1, B = p->batch;
+    float2* x = (float2*)in;
+    if (!xpose) {
+        if (run_col(p, p->ax0, +1, x, p->P, p->P, B, p->M, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_col(p, p->ax1, +1, x, H, H, B * n0, n1 * H, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_row(p, +1, x, out, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        return FFT3D_OK;
+    }
+    float2* w = (float2*)p->workspace;
+    if (!(p->flags & FFT3D_FLAG_TRANSPOSE_BACK)) {
+        // input is (n1, n0, H): n0 pass on the middle axis, transpose back to (n0, n1, H)
+        if (run_col(p, p->ax0, +1, x, H, H, B * n1, n0 * H, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_swap(p, x, w, n1, n0, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_col(p, p->ax1, +1, w, H, H, B * n0, n1 * H, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_row(p, +1, w, out, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+    } else {
+        if (run_swap(p, x, w, n0, n1, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_col(p, p->ax0, +1, w, H, H, B * n1, n0 * H, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_swap(p, w, x, n1, n0, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_col(p, p->ax1, +1, x, H, H, B * n0, n1 * H, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_row(p, +1, x, out, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+    }
+    return FFT3D_OK;
+}
+
+int fft3d_set_profiling(fft3d_handle p, int enable)
+{
+    if (!p) return fail(FFT3D_ERR_INVALID_ARG);
+    p->profiling = enable != 0;
+    return FFT3D_OK;
+}
+
+int fft3d_profile_read(fft3d_handle p, double* ms, int* count, int n)
+{
+    if (!p || n < 0 || (n > 0 && (!ms || !count))) return fail(FFT3D_ERR_INVALID_ARG);
+    for (int i = 0; i < n; ++i) {
+        ms[i] = 0.0;
+        count[i] = 0;
+    }
+    int st = FFT3D_OK;
+    for (size_t i = 0; i < p->prof_used; ++i) {
+        ProfRecord& r = p->prof[i];
+        float t = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) {
+            st = FFT3D_ERR_CUDA;
+            continue;
+        }
+        if (r.pass < n) {
+            ms[r.pass] += t;
+            count[r.pass] += 1;
+        }
+    }
+    p->prof_used = 0;
+    return st == FFT3D_OK ? FFT3D_OK : fail(st);
+}
+
+const char* fft3d_pass_name(int pass)
+{
+    return (pass >= 0 && pass < PASS_COUNT) ? kPassNames[pass] : nullptr;
+}
+
+double fft3d_pass_bytes(fft3d_handle p, int pass)
+{
+    if (!p) return 0.0;
+    const double B = p->batch, real = 4.0 * (double)p->N * B, cplx = 8.0 * (double)p->M * B;
+    switch (pass) {
+    case PASS_ROW_R2C:
+    case PASS_ROW_C2R: return real + cplx;
+    case PASS_N1_FWD:
+    case PASS_N1_INV: return p->n1 > 1 ? 2.0 * cplx : 0.0;
+    case PASS_N0_FWD:
+    case PASS_N0_INV: return p->n0 > 1 ? 2.0 * cplx : 0.0;
+    case PASS_SWAP01: return 2.0 * cplx;
+    default: return 0.0;
+    }
+}
+
+}  // extern "C"

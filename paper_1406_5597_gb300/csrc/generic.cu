@@ -1,0 +1,198 @@
+// Runtime-length kernels: any transform length whose prime factors are 2, 3
+// and 5 (up to 4096), for the axis lengths that have no compile-time
+// specialisation.  A CTA stages G lines in shared memory (two buffers) and
+// runs the Stockham stages of a runtime radix list, one butterfly per thread
+// iteration.  Same mathematics as the specialised kernels (see stockham.cuh
+// and kernels.cuh); slower, but length-agnostic.
+#include "args.h"
+#include "radix.cuh"
+
+namespace fft3d {
+
+namespace {
+
+// Index of position p of line g in a buffer of G interleaved lines.
+__device__ __forceinline__ int gi(int p, int g, int G) { return p * G + g; }
+
+// Runs every stage of g.radix on the G lines in buf[0]; returns the buffer
+// that holds the result (natural order).
+template <int DIR>
+__device__ float2* generic_stages(const GenPlan& g, float2* b0, float2* b1, int G, const float2* __restrict__ tw)
+{
+    const int L = g.L;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthr = blockDim.x * blockDim.y;
+    float2* src = b0;
+    float2* dst = b1;
+    int Ns = 1;
+    for (int s = 0; s < g.nst; ++s) {
+        const int R = g.radix[s];
+        const int nbf = L / R;
+        const int step = L / (Ns * R);
+        for (int i = tid; i < nbf * G; i += nthr) {
+            const int line = i % G;
+            const int j = i / G;
+            const int jm = j % Ns;
+            float2 a[16];
+            for (int k = 0; k < R; ++k) {
+                float2 x = src[gi(j + k * nbf, line, G)];
+                if (k > 0 && Ns > 1) x = twiddle<DIR>(x, __ldg(&tw[k * jm * step]));
+                a[k] = x;
+            }
+            dft_runtime<DIR>(R, a);
+            const int base = (j / Ns) * Ns * R + jm;
+            for (int k = 0; k < R; ++k) dst[gi(base + k * Ns, line, G)] = a[k];
+        }
+        __syncthreads();
+        float2* t = src;
+        src = dst;
+        dst = t;
+        Ns *= R;
+    }
+    return src;
+}
+
+template <int DIR>
+__global__ void generic_col_kernel(ColArgs a, GenPlan g, int G)
+{
+    extern __shared__ float2 sm[];
+    const int L = g.L;
+    float2* b0 = sm;
+    float2* b1 = sm + (size_t)L * G;
+    const long long ctiles = (a.C + G - 1) / G;
+    const long long b = blockIdx.x / ctiles;
+    const long long c0 = (blockIdx.x - b * ctiles) * G;
+    float2* base = a.data + b * a.Bs + c0;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthr = blockDim.x * blockDim.y;
+    for (int i = tid; i < L * G; i += nthr) {
+        const int line = i % G, p = i / G;
+        b0[gi(p, line, G)] = (c0 + line < a.C) ? base[(long long)p * a.S + line] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2* res = generic_stages<DIR>(g, b0, b1, G, a.tw);
+    for (int i = tid; i < L * G; i += nthr) {
+        const int line = i % G, p = i / G;
+        if (c0 + line < a.C) base[(long long)p * a.S + line] = cscale(res[gi(p, line, G)], a.scale);
+    }
+}
+
+// Rows: G contiguous rows per CTA.  DIR = -1: r2c (packed row in, H bins
+// out); DIR = +1: c2r (H bins in, packed real row out).  Buffers hold L+1
+// positions per line so that the unpacked H = L+1 bins fit.
+template <int DIR>
+__global__ void generic_row_kernel(RowArgs a, GenPlan g, int G)
+{
+    extern __shared__ float2 sm[];
+    const int L = g.L, H = L + 1;
+    float2* b0 = sm;
+    float2* b1 = sm + (size_t)H * G;
+    const long long row0 = (long long)blockIdx.x * G;
+    const int nrows = (int)min((long long)G, a.rows - row0);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthr = blockDim.x * blockDim.y;
+    if (DIR < 0) {
+        const float2* in = reinterpret_cast<const float2*>(a.in) + row0 * L;
+        for (int i = tid; i < L * G; i += nthr) {
+            const int line = i / L, p = i % L;
+            b0[gi(p, line, G)] = line < nrows ? in[i] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        float2* Z = generic_stages<-1>(g, b0, b1, G, a.tw);
+        float2* X = (Z == b0) ? b1 : b0;
+        for (int i = tid; i < H * G; i += nthr) {
+            const int line = i % G, k = i / G;
+            float2 r;
+            if (k == L) {
+                const float2 z0 = Z[gi(0, line, G)];
+                r = make_float2(z0.x - z0.y, 0.f);
+            } else {
+                const float2 zk = Z[gi(k, line, G)];
+                const float2 zc = cconj(Z[gi(k == 0 ? 0 : L - k, line, G)]);
+                const float2 s = cadd(zk, zc), d = csub(zk, zc);
+                const float2 wd = cmul(d, __ldg(&a.twpack[k]));
+                r = make_float2(0.5f * (s.x + wd.y), 0.5f * (s.y - wd.x));
+            }
+            X[gi(k, line, G)] = r;
+        }
+        __syncthreads();
+        float2* out = reinterpret_cast<float2*>(a.out) + row0 * H;
+        for (int i = tid; i < H * nrows; i += nthr) {
+            const int line = i / H, k = i % H;
+            out[i] = X[gi(k, line, G)];
+        }
+    } else {
+        const float2* in = reinterpret_cast<const float2*>(a.in) + row0 * H;
+        for (int i = tid; i < H * G; i += nthr) {
+            const int line = i / H, k = i % H;
+            b1[gi(k, line, G)] = line < nrows ? in[i] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int i = tid; i < L * G; i += nthr) {
+            const int line = i % G, k = i / G;
+            float2 xk = b1[gi(k, line, G)];
+            float2 xc = cconj(b1[gi(L - k, line, G)]);
+            if (k == 0) {
+                xk.y = 0.f;
+                xc.y = 0.f;
+            }
+            const float2 s = cadd(xk, xc), d = csub(xk, xc);
+            const float2 wd = cmulc(d, __ldg(&a.twpack[k]));
+            b0[gi(k, line, G)] = make_float2(s.x - wd.y, s.y + wd.x);
+        }
+        __syncthreads();
+        float2* z = generic_stages<+1>(g, b0, b1, G, a.tw);
+        float2* out = reinterpret_cast<float2*>(a.out) + row0 * L;
+        for (int i = tid; i < L * nrows; i += nthr) {
+            const int line = i / L, p = i % L;
+            out[i] = z[gi(p, line, G)];
+        }
+    }
+}
+
+int lines_per_cta(int L)
+{
+    const int cap = 64 * 1024;  // bytes of shared memory for both buffers
+    int G = cap / (2 * (L + 1) * (int)sizeof(float2));
+    if (G > 32) G = 32;
+    if (G < 1) G = 1;
+    return G;
+}
+
+}  // namespace
+
+cudaError_t generic_col(const ColArgs& a, const GenPlan& g, int dir, cudaStream_t s)
+{
+    const int G = lines_per_cta(g.L);
+    const size_t smem = 2 * (size_t)(g.L + 1) * G * sizeof(float2);
+    const long long tiles = a.nb * ((a.C + G - 1) / G);
+    if (tiles <= 0) return cudaSuccess;
+    dim3 block(G, 256 / G > 0 ? 256 / G : 1);
+    if (dir < 0) {
+        cudaFuncSetAttribute(generic_col_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        generic_col_kernel<-1><<<(unsigned)tiles, block, smem, s>>>(a, g, G);
+    } else {
+        cudaFuncSetAttribute(generic_col_kernel<+1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        generic_col_kernel<+1><<<(unsigned)tiles, block, smem, s>>>(a, g, G);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t generic_row(const RowArgs& a, const GenPlan& g, int dir, cudaStream_t s)
+{
+    const int G = lines_per_cta(g.L);
+    const size_t smem = 2 * (size_t)(g.L + 1) * G * sizeof(float2);
+    const long long blocks = (a.rows + G - 1) / G;
+    if (blocks <= 0) return cudaSuccess;
+    dim3 block(G, 256 / G > 0 ? 256 / G : 1);
+    if (dir < 0) {
+        cudaFuncSetAttribute(generic_row_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        generic_row_kernel<-1><<<(unsigned)blocks, block, smem, s>>>(a, g, G);
+    } else {
+        cudaFuncSetAttribute(generic_row_kernel<+1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        generic_row_kernel<+1><<<(unsigned)blocks, block, smem, s>>>(a, g, G);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fft3d

@@ -146,38 +146,42 @@ def spectral_velocity(n0: int, n1: int, n2: int, seed: int, components=(0, 1, 2)
     out = np.zeros((len(comps), n0, n1, H), dtype=np.complex128)
     energy = np.zeros(3)
 
+    w = np.full(H, 2.0)
+    w[0] = w[H - 1] = 1.0
     for a0 in range(0, n0, plane_chunk):
         b0 = min(n0, a0 + plane_chunk)
         K0 = k0v[a0:b0, None, None]
         K1 = k1v[None, :, None]
         K2 = k2v[None, None, :]
         kk = K0 * K0 + K1 * K1 + K2 * K2
-        kmag = np.sqrt(kk)
-        with np.errstate(divide="ignore", invalid="ignore"):
-            amp = np.where(kk > 0, np.sqrt(energy_shape(kmag) / (4.0 * np.pi * np.where(kk > 0, kk, 1.0))), 0.0)
-        zero = ny0[a0:b0, None, None] | ny1[None, :, None] | ny2[None, None, :] | (9.0 * kk >= nmin * nmin)
-        amp = np.where(zero, 0.0, amp)
-        shape = (b0 - a0, n1, H)
-        m = (np.arange(a0, b0, dtype=np.uint64)[:, None, None] * np.uint64(n1)
-             + np.arange(n1, dtype=np.uint64)[None, :, None]) * np.uint64(H) \
-            + np.arange(H, dtype=np.uint64)[None, None, :]
+        zero = ny0[a0:b0, None, None] | ny1[None, :, None] | ny2[None, None, :] | (9.0 * kk >= nmin * nmin) \
+            | (kk == 0)
+        # only the modes that survive steps 1 and 5 are drawn (the others are 0)
+        idx = np.flatnonzero(~zero)
+        if idx.size == 0:
+            continue
+        kkf = kk.ravel()[idx] if kk.size == zero.size else np.broadcast_to(kk, zero.shape).ravel()[idx]
+        i0, rest = np.divmod(idx, n1 * H)
+        i1, i2 = np.divmod(rest, H)
+        q0, q1, q2 = k0v[a0 + i0], k1v[i1], k2v[i2]
+        amp = np.sqrt(energy_shape(np.sqrt(kkf)) / (4.0 * np.pi * kkf))
+        m = ((np.uint64(a0) + i0.astype(np.uint64)) * np.uint64(n1) + i1.astype(np.uint64)) * np.uint64(H) \
+            + i2.astype(np.uint64)
         a = []
         for c in range(3):
             th = 2.0 * np.pi * uniform01(seed, m * np.uint64(3) + np.uint64(c))
-            a.append(amp * np.exp(1j * th))
-        kdota = K0 * a[0] + K1 * a[1] + K2 * a[2]
-        with np.errstate(divide="ignore", invalid="ignore"):
-            f = np.where(kk > 0, kdota / np.where(kk > 0, kk, 1.0), 0.0)
-        kvec = (K0, K1, K2)
+            a.append(amp * (np.cos(th) + 1j * np.sin(th)))
+        f = (q0 * a[0] + q1 * a[1] + q2 * a[2]) / kkf
+        kvec = (q0, q1, q2)
+        wt = w[i2]
         for c in range(3):
-            uc = a[c] - np.broadcast_to(kvec[c], shape) * f
-            w = np.full(H, 2.0)
-            w[0] = w[H - 1] = 1.0
-            # chunk energy (the k2 = 0 plane is rebuilt below; it is recounted there)
-            energy[c] += float(np.sum((uc.real ** 2 + uc.imag ** 2)[:, :, 1:] * w[1:]))
+            uc = a[c] - kvec[c] * f
+            # energy of the chunk (the k2 = 0 plane is rebuilt below and recounted there)
+            energy[c] += float(np.sum((uc.real ** 2 + uc.imag ** 2) * np.where(i2 > 0, wt, 0.0)))
             if c in comps:
-                out[comps.index(c), a0:b0] = uc
-        del a, kdota, f
+                dst = out[comps.index(c), a0:b0].reshape(-1)
+                dst[idx] = uc
+        del a, f
 
     # Hermitian consistency on the k2 = 0 plane (step 6).
     for i in range(len(comps)):

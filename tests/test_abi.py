@@ -1,0 +1,61 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function
+include/fft3d.h declares; host-side argument checks answer without a GPU."""
+import ctypes
+
+import pytest
+
+import paper_1406_5597_gb300 as fft3d
+
+
+@pytest.fixture(scope="module")
+def lib():
+    fft3d.build()
+    return fft3d.load()
+
+
+def test_exports_every_declared_function(lib):
+    names = fft3d.declared_functions()
+    assert "fft3d_plan" in names and "fft3d_r2c" in names and "fft3d_c2r" in names
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in fft3d._SIGS, n
+
+
+def test_error_strings(lib):
+    for st in range(0, 8):
+        assert fft3d.fft3d_error_string(st)
+    assert "unknown" in fft3d.fft3d_error_string(99)
+
+
+@pytest.mark.parametrize("dims,status", [
+    ((0, 8, 8), fft3d.FFT3D_ERR_INVALID_ARG),
+    ((8, 8, 1), fft3d.FFT3D_ERR_INVALID_ARG),
+    ((8, 8, 7), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),   # odd n2
+    ((14, 8, 8), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),  # factor 7
+    ((8, 8, 22), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),  # n2/2 = 11
+    ((8192, 8, 8), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),
+])
+def test_plan_rejects_bad_sizes_before_touching_the_device(lib, dims, status):
+    assert not fft3d.fft3d_plan(*dims, fft3d.FFT3D_F32, 1)
+    assert fft3d.fft3d_last_error() == status
+
+
+def test_plan_rejects_bad_dtype_batch_flags(lib):
+    assert not fft3d.fft3d_plan(8, 8, 8, 7, 1)
+    assert fft3d.fft3d_last_error() == fft3d.FFT3D_ERR_INVALID_ARG
+    assert not fft3d.fft3d_plan(8, 8, 8, 0, 0)
+    assert fft3d.fft3d_last_error() == fft3d.FFT3D_ERR_INVALID_ARG
+    assert not fft3d.fft3d_plan_variant(8, 8, 8, 0, 1, fft3d.FFT3D_FLAG_TRANSPOSE_BACK)
+    assert fft3d.fft3d_last_error() == fft3d.FFT3D_ERR_INVALID_ARG
+    assert not fft3d.fft3d_plan_variant(8, 8, 8, 0, 1, 0x100)
+
+
+def test_null_handles(lib):
+    assert fft3d.fft3d_r2c(None, 16, 32) == fft3d.FFT3D_ERR_INVALID_ARG
+    assert fft3d.fft3d_c2r(None, 16, 32) == fft3d.FFT3D_ERR_INVALID_ARG
+    assert fft3d.fft3d_workspace_bytes(None) == 0
+    assert fft3d.fft3d_set_workspace(None, 0) == fft3d.FFT3D_ERR_INVALID_ARG
+    assert fft3d.fft3d_launches_per_call(None) == fft3d.FFT3D_ERR_INVALID_ARG
+    fft3d.fft3d_destroy(None)
+    buf = ctypes.create_string_buffer(8)
+    assert lib.fft3d_describe(None, buf, 8) == fft3d.FFT3D_ERR_INVALID_ARG

@@ -1,0 +1,253 @@
+"""GPU parity: the CUDA path against the FP64 oracle, element by element, on
+seeded inputs, through the C ABI (ctypes binding; torch provides only device
+memory and the stream).
+
+Tolerance (FP32 storage and arithmetic): relative L2 over all real and
+imaginary components, accumulated in FP64, <= 5e-6 per direction and <= 1e-5
+for the round trip.  The forward result is compared with the oracle's r2c of
+the SAME FP32-rounded input promoted to FP64; the inverse with the oracle's
+c2r of the SAME complex64 input, so the two directions' errors stay apart.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 5e-6
+TOL_RT = 1e-5
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.complex128 if np.iscomplexobj(a) or np.iscomplexobj(b) else np.float64)
+    b = np.asarray(b, dtype=a.dtype)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def gpu_r2c(lib, x32, flags=0, batch=None):
+    """x32: (n0, n1, n2) or (batch, n0, n1, n2) float32 numpy -> complex128 numpy."""
+    n0, n1, n2 = x32.shape[-3:]
+    b = 1 if x32.ndim == 3 else x32.shape[0]
+    plan = lib.Plan(n0, n1, n2, lib.FFT3D_F32, b, flags)
+    xd = torch.from_numpy(np.ascontiguousarray(x32)).cuda()
+    H = n2 // 2 + 1
+    lead = x32.shape[:-3]
+    oshape = lead + ((n1, n0, H) if (flags & lib.FFT3D_FLAG_EXPLICIT_TRANSPOSE and not flags & lib.FFT3D_FLAG_TRANSPOSE_BACK)
+                     else (n0, n1, H))
+    out = torch.empty(oshape, dtype=torch.complex64, device="cuda")
+    plan.r2c(xd.data_ptr(), out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert lib.fft3d_query_device_status(plan.handle) == lib.FFT3D_OK
+    return out.cpu().numpy().astype(np.complex128)
+
+
+def gpu_c2r(lib, Y64, n2, flags=0):
+    """Y64: complex64 numpy (n0, n1, H) (or transposed per flags), batch-leading allowed."""
+    if flags & lib.FFT3D_FLAG_EXPLICIT_TRANSPOSE and not flags & lib.FFT3D_FLAG_TRANSPOSE_BACK:
+        n1, n0 = Y64.shape[-3], Y64.shape[-2]
+    else:
+        n0, n1 = Y64.shape[-3], Y64.shape[-2]
+    b = 1 if Y64.ndim == 3 else Y64.shape[0]
+    plan = lib.Plan(n0, n1, n2, lib.FFT3D_F32, b, flags)
+    Yd = torch.from_numpy(np.ascontiguousarray(Y64)).cuda()
+    out = torch.empty(Y64.shape[:-3] + (n0, n1, n2), dtype=torch.float32, device="cuda")
+    plan.c2r(Yd.data_ptr(), out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def random_half_spectrum(shape, seed):
+    n0, n1, H = shape
+    re = synth.uniform_field(shape, seed)
+    im = synth.uniform_field(shape, seed + 1)
+    return (re + 1j * im).astype(np.complex64)
+
+
+# ---------------------------------------------------------------------------
+# The tiny configuration: 32^3, uniform[-1, 1), seed 1407.
+# ---------------------------------------------------------------------------
+
+def test_config1_forward_inverse_roundtrip(cuda_lib):
+    n = 32
+    x32 = synth.uniform_field((n, n, n), synth.seed_for_config(1)).astype(np.float32)
+    X = gpu_r2c(cuda_lib, x32)
+    Xo = oracle.r2c3d(x32.astype(np.float64))
+    assert rel_l2(X, Xo) <= TOL
+    # inverse of the same complex64 input as the oracle
+    Y = X.astype(np.complex64)
+    y = gpu_c2r(cuda_lib, Y, n)
+    assert rel_l2(y, oracle.c2r3d(Y.astype(np.complex128), n)) <= TOL
+    # round trip x N
+    assert rel_l2(y / n ** 3, x32.astype(np.float64)) <= TOL_RT
+    # Parseval on the GPU spectrum
+    e = oracle.half_energy(X, n) / n ** 3
+    assert abs(e - np.sum(x32.astype(np.float64) ** 2)) <= 1e-5 * e
+    # Hermitian symmetry of the k2 = 0 and k2 = n2/2 planes
+    for k2 in (0, n // 2):
+        P = X[:, :, k2]
+        mirror = np.conj(P[(-np.arange(n)) % n][:, (-np.arange(n)) % n])
+        assert np.linalg.norm(P - mirror) <= TOL * np.linalg.norm(X)
+
+
+@pytest.mark.parametrize("k", [(1, 0, 0), (0, 3, 5), (7, -2, 16), (0, 0, 16), (16, 16, 0), (-5, 11, 9)])
+def test_config1_single_modes(cuda_lib, k):
+    n = 32
+    x32 = synth.cosine_mode(n, n, n, *k).astype(np.float32)
+    X = gpu_r2c(cuda_lib, x32)
+    Xo = oracle.r2c3d(x32.astype(np.float64))
+    assert rel_l2(X, Xo) <= TOL
+    # the spike: N/2 at k (and at -k on the k2 = 0 / n2/2 planes), N at self-conjugate k
+    kp = tuple(v % n for v in k)
+    expect = n ** 3 / 2 * (2 if tuple((-v) % n for v in k) == kp else 1)
+    assert abs(X[kp] - expect) <= 1e-4 * n ** 3
+
+
+def test_config1_delta(cuda_lib):
+    n = 32
+    x32 = synth.delta_field(n, n, n, 3, 5, 7).astype(np.float32)
+    X = gpu_r2c(cuda_lib, x32)
+    assert rel_l2(X, oracle.r2c3d(x32.astype(np.float64))) <= TOL
+
+
+# ---------------------------------------------------------------------------
+# Shapes: specialised lengths (2^k, 3*2^k, 5*2^k), runtime-generic lengths,
+# non-cubic shapes, unit axes, odd H (ragged column tiles), long axes.
+# ---------------------------------------------------------------------------
+SHAPES = [
+    (8, 8, 8), (16, 16, 16), (64, 64, 64), (128, 128, 128), (256, 64, 32), (64, 256, 512),
+    (48, 80, 96), (96, 96, 96), (160, 32, 160), (192, 48, 64), (64, 64, 192),
+    (6, 10, 16), (15, 12, 10), (30, 20, 24), (2, 2, 2), (1, 1, 2), (1, 8, 16), (4, 1, 8), (5, 3, 2),
+    (1536, 2, 4), (2048, 2, 4), (2, 2048, 4), (4, 4, 2048), (2, 3, 4096), (1024, 8, 8), (8, 1024, 8),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_shapes_forward_and_inverse(cuda_lib, shape):
+    n0, n1, n2 = shape
+    x32 = synth.uniform_field(shape, seed=17).astype(np.float32)
+    X = gpu_r2c(cuda_lib, x32)
+    assert rel_l2(X, oracle.r2c3d(x32.astype(np.float64))) <= TOL
+    Y = random_half_spectrum((n0, n1, n2 // 2 + 1), seed=23)
+    y = gpu_c2r(cuda_lib, Y, n2)
+    assert rel_l2(y, oracle.c2r3d(Y.astype(np.complex128), n2)) <= TOL
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (48, 80, 96), (64, 64, 64)], ids=lambda s: "x".join(map(str, s)))
+def test_generic_kernels_forced(cuda_lib, shape):
+    n0, n1, n2 = shape
+    f = cuda_lib.FFT3D_FLAG_GENERIC
+    x32 = synth.uniform_field(shape, seed=29).astype(np.float32)
+    assert rel_l2(gpu_r2c(cuda_lib, x32, flags=f), oracle.r2c3d(x32.astype(np.float64))) <= TOL
+    Y = random_half_spectrum((n0, n1, n2 // 2 + 1), seed=31)
+    assert rel_l2(gpu_c2r(cuda_lib, Y, n2, flags=f), oracle.c2r3d(Y.astype(np.complex128), n2)) <= TOL
+
+
+def test_batch_entries_do_not_bleed(cuda_lib):
+    shape = (3, 16, 24, 20)
+    x32 = synth.uniform_field(shape, seed=37).astype(np.float32)
+    X = gpu_r2c(cuda_lib, x32)
+    for b in range(3):
+        assert rel_l2(X[b], oracle.r2c3d(x32[b].astype(np.float64))) <= TOL
+    Y = random_half_spectrum((3 * 16, 24, 11), seed=41).reshape(3, 16, 24, 11)
+    y = gpu_c2r(cuda_lib, Y, 20)
+    for b in range(3):
+        assert rel_l2(y[b], oracle.c2r3d(Y[b].astype(np.complex128), 20)) <= TOL
+
+
+def test_impulses_map_to_plane_waves(cuda_lib):
+    """A delta at (j0, j1, j2) transforms to exp(-2 pi i k.j/n): checks every
+    index placement, including the rows and columns at the tile edges."""
+    shape = (24, 40, 36)
+    for j in [(0, 0, 0), (23, 39, 35), (5, 17, 1), (12, 20, 18)]:
+        x32 = synth.delta_field(*shape, *j).astype(np.float32)
+        X = gpu_r2c(cuda_lib, x32)
+        assert rel_l2(X, oracle.r2c3d(x32.astype(np.float64))) <= TOL
+
+
+def test_c2r_ignores_imag_of_dc_and_nyquist_bins(cuda_lib):
+    n0, n1, n2 = 8, 12, 16
+    Y = random_half_spectrum((n0, n1, n2 // 2 + 1), seed=43)
+    y = gpu_c2r(cuda_lib, Y, n2)
+    assert rel_l2(y, oracle.c2r3d(Y.astype(np.complex128), n2)) <= TOL
+    assert rel_l2(y, oracle.c2r3d_naive(Y.astype(np.complex128), n2)) <= TOL
+
+
+@pytest.mark.parametrize("back", [False, True])
+def test_explicit_transpose_variant(cuda_lib, back):
+    n0, n1, n2 = 32, 48, 40
+    f = cuda_lib.FFT3D_FLAG_EXPLICIT_TRANSPOSE | (cuda_lib.FFT3D_FLAG_TRANSPOSE_BACK if back else 0)
+    x32 = synth.uniform_field((n0, n1, n2), seed=47).astype(np.float32)
+    X = gpu_r2c(cuda_lib, x32, flags=f)
+    Xo = oracle.r2c3d(x32.astype(np.float64))
+    assert rel_l2(X, Xo if back else Xo.transpose(1, 0, 2)) <= TOL
+    Y = random_half_spectrum((n0, n1, n2 // 2 + 1), seed=53)
+    yo = oracle.c2r3d(Y.astype(np.complex128), n2)
+    Yin = Y if back else np.ascontiguousarray(Y.transpose(1, 0, 2))
+    assert rel_l2(gpu_c2r(cuda_lib, Yin, n2, flags=f), yo) <= TOL
+
+
+def test_argument_errors_leave_output_untouched(cuda_lib):
+    lib = cuda_lib
+    plan = lib.Plan(8, 8, 8)
+    x = torch.zeros(8 * 8 * 8 + 8, dtype=torch.float32, device="cuda")
+    out = torch.full((8 * 8 * 5 * 2 + 8,), 7.0, dtype=torch.float32, device="cuda")
+    assert lib.fft3d_r2c(plan.handle, x.data_ptr() + 4, out.data_ptr()) == lib.FFT3D_ERR_MISALIGNED
+    assert lib.fft3d_r2c(plan.handle, x.data_ptr(), x.data_ptr() + 16) == lib.FFT3D_ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert bool((out == 7.0).all())
+    xp = lib.fft3d_plan_variant(8, 8, 8, 0, 1, lib.FFT3D_FLAG_EXPLICIT_TRANSPOSE)
+    assert lib.fft3d_workspace_bytes(xp) == 8 * 8 * 5 * 8
+    assert lib.fft3d_r2c(xp, x.data_ptr(), out.data_ptr()) == lib.FFT3D_ERR_NO_WORKSPACE
+    assert lib.fft3d_set_workspace(xp, out.data_ptr() + 16) == lib.FFT3D_ERR_MISALIGNED
+    lib.fft3d_destroy(xp)
+
+
+# ---------------------------------------------------------------------------
+# Full size of the benchmark workload: 512^3 spectrum-shaped field (seed 1408).
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def field512():
+    n = 512
+    S = synth.spectral_velocity(n, n, n, seed=synth.seed_for_config(2), components=(0,))[0]
+    x = oracle.c2r3d(S, n)
+    return S, x
+
+
+@pytest.mark.parametrize("flags", [0, 1, 3], ids=["transpose-free", "explicit-transpose", "transpose-back"])
+def test_512_spectrum_as_oracle_and_spot_bins(cuda_lib, field512, flags):
+    """x = c2r(S) exactly (FP64), so r2c(x) = N S up to the FP32 rounding of x
+    (~3e-8 relative): a full-size reference that needs no 512^3 forward oracle.
+    Plus exact FP64 spot bins of the same FP32 input."""
+    S, x = field512
+    n = 512
+    N = n ** 3
+    x32 = x.astype(np.float32)
+    X = gpu_r2c(cuda_lib, x32, flags=flags)
+    if flags == 1:
+        X = X.transpose(1, 0, 2)
+    assert rel_l2(X, N * S) <= TOL
+    rng = np.random.default_rng(5)
+    ks = np.stack([rng.integers(0, n, 12), rng.integers(0, n, 12), rng.integers(0, n // 2 + 1, 12)], 1)
+    ks = np.concatenate([ks, [[0, 0, 0], [4, 3, 0], [511, 1, 256], [1, 2, 3]]])
+    ref = oracle.r2c_bins_f32(x32, ks)
+    got = np.array([X[tuple(k)] for k in ks])
+    scale = np.sqrt(np.mean(np.abs(X) ** 2))
+    assert np.max(np.abs(got - ref)) <= 2e-5 * scale
+
+
+def test_512_inverse(cuda_lib, field512):
+    S, x = field512
+    n = 512
+    N = n ** 3
+    Y = (N * S).astype(np.complex64)
+    y = gpu_c2r(cuda_lib, Y, n)
+    assert rel_l2(y, N * x) <= TOL
+    rng = np.random.default_rng(6)
+    js = np.stack([rng.integers(0, n, 8), rng.integers(0, n, 8), rng.integers(0, n, 8)], 1)
+    ref = oracle.c2r_points_c64(Y, n, js)
+    got = np.array([y[tuple(j)] for j in js])
+    assert np.max(np.abs(got - ref)) <= 2e-5 * np.sqrt(np.mean(y ** 2))
