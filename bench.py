@@ -107,7 +107,7 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -204,7 +204,7 @@ def time_steps(fn, stream, steps):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fft3d", choices=["fft3d", "reference"])
     ap.add_argument("--n", type=int, default=512)
@@ -257,7 +257,7 @@ def main():
     torch.cuda.synchronize()
     sampler = ClockSampler(local_rank)
     sampler.start()
-    time.sleep(0.3)
+    time.sleep(1.0)
     fft3d.fft3d_set_profiling(plan.handle, True)
     ms_total = time_steps(step, stream, args.steps)
     fft3d.fft3d_set_profiling(plan.handle, False)

@@ -235,8 +235,9 @@ def test_512_spectrum_as_oracle_and_spot_bins(cuda_lib, field512, flags):
     ks = np.concatenate([ks, [[0, 0, 0], [4, 3, 0], [511, 1, 256], [1, 2, 3]]])
     ref = oracle.r2c_bins_f32(x32, ks)
     got = np.array([X[tuple(k)] for k in ks])
-    scale = np.sqrt(np.mean(np.abs(X) ** 2))
-    assert np.max(np.abs(got - ref)) <= 2e-5 * scale
+    # per-bin bound: relative to the bin, with the field's rms as floor
+    scale = np.abs(ref) + np.sqrt(np.mean(np.abs(X) ** 2))
+    assert np.all(np.abs(got - ref) <= TOL * scale)
 
 
 def test_512_inverse(cuda_lib, field512):
@@ -250,4 +251,4 @@ def test_512_inverse(cuda_lib, field512):
     js = np.stack([rng.integers(0, n, 8), rng.integers(0, n, 8), rng.integers(0, n, 8)], 1)
     ref = oracle.c2r_points_c64(Y, n, js)
     got = np.array([y[tuple(j)] for j in js])
-    assert np.max(np.abs(got - ref)) <= 2e-5 * np.sqrt(np.mean(y ** 2))
+    assert np.all(np.abs(got - ref) <= TOL * (np.abs(ref) + np.sqrt(np.mean(y ** 2))))
