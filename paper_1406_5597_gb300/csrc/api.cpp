@@ -19,6 +19,7 @@
 
 #include "args.h"
 #include "fft3d.h"
+#include "tma_host.h"
 
 namespace fft3d {
 const LenEntry* entries_small(int* n);
@@ -150,6 +151,13 @@ struct fft3d_plan_s {
     bool profiling = false;
     std::vector<ProfRecord> prof;  // event pairs, reused across reads
     size_t prof_used = 0;
+    // tensor maps of recent column-pass operands, keyed by (base, stride)
+    struct MapCache {
+        const void* base = nullptr;
+        long long S = 0;
+        CUtensorMap map;
+    } maps[4];
+    int next_map = 0;
 };
 
 namespace {
@@ -206,14 +214,42 @@ bool uses_generic(const fft3d_plan_s* p, const Axis& a, bool row)
     return row ? (a.spec->r2c == nullptr) : false;
 }
 
+// The TMA column kernel needs a 2D tensor view: batch entries stacked as rows
+// (Bs == L*S), row byte stride 8*S a multiple of 16, C*8 rows of at least one box.
+bool tma_ok(const fft3d_plan_s* p, const Axis& a, long long S, long long C, long long Bs)
+{
+    if (p->flags & (FFT3D_FLAG_GENERIC | FFT3D_FLAG_THREE_PASS)) return false;
+    if (!a.spec || !a.spec->tma_W) return false;
+    return Bs == (long long)a.L * S && (S % 2) == 0 && C >= a.spec->tma_W;
+}
+
+const CUtensorMap* tensor_map(fft3d_plan_s* p, const Axis& a, const ColArgs& ca)
+{
+    for (auto& m : p->maps)
+        if (m.base == ca.data && m.S == ca.S) return &m.map;
+    auto& m = p->maps[p->next_map];
+    p->next_map = (p->next_map + 1) % 4;
+    if (col_tensor_map_host(&m.map, ca, a.L, a.spec->tma_W) != cudaSuccess) {
+        m.base = nullptr;
+        return nullptr;
+    }
+    m.base = ca.data;
+    m.S = ca.S;
+    return &m.map;
+}
+
 cudaError_t run_col(fft3d_plan_s* p, const Axis& a, int dir, float2* data, long long S, long long C,
                     long long nb, long long Bs, cudaStream_t s)
 {
     if (a.L <= 1) return cudaSuccess;
     const bool n0axis = (&a == &p->ax0);
     ProfScope ps(p, n0axis ? (dir < 0 ? PASS_N0_FWD : PASS_N0_INV) : (dir < 0 ? PASS_N1_FWD : PASS_N1_INV), s);
-    ColArgs ca{data, S, C, nb, Bs, a.d_tw, 1.0f};
+    ColArgs ca{data, S, C, nb, Bs, a.d_tw, 1.0f, p->d_status};
     if (uses_generic(p, a, false)) return generic_col(ca, a.gen, dir, s);
+    if (tma_ok(p, a, S, C, Bs)) {
+        if (const CUtensorMap* m = tensor_map(p, a, ca))
+            return dir < 0 ? a.spec->tma_fwd(ca, *m, s) : a.spec->tma_inv(ca, *m, s);
+    }
     return dir < 0 ? a.spec->col_fwd(ca, s) : a.spec->col_inv(ca, s);
 }
 
@@ -232,7 +268,10 @@ std::string axis_desc(const fft3d_plan_s* p, const Axis& a, bool row)
     if (uses_generic(p, a, row)) {
         std::snprintf(b, sizeof b, "generic L=%d", a.L);
     } else if (row) {
-        std::snprintf(b, sizeof b, "L=%d E=%d rows/CTA=%d", a.L, a.spec->row_E, a.spec->row_rows);
+        std::snprintf(b, sizeof b, "L=%d E=%d rows/CTA=%d %s", a.L, a.spec->row_E, a.spec->row_rows,
+                      a.spec->row_warp ? "warp" : "smem");
+    } else if (&a == &p->ax0 && a.spec->tma_W && !(p->flags & FFT3D_FLAG_THREE_PASS)) {
+        std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d tma", a.L, a.spec->tma_E, a.spec->tma_W);
     } else {
         std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d", a.L, a.spec->col_E, a.spec->col_W);
     }

@@ -1,6 +1,7 @@
 // Kernel argument blocks and the launcher registry shared by the device
 // translation units and the host planner.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace fft3d {
@@ -13,7 +14,11 @@ struct ColArgs {
     long long Bs;        // batch stride (complex elements)
     const float2* tw;    // W_L^m, m in [0, L)
     float scale;         // multiplies the result (1 for a plain pass)
+    int* status;         // device status word (bounded waits that give up set bits here)
 };
+
+// Device status bits.
+constexpr int kStatusTimeout = 1;
 
 struct RowArgs {
     const void* in;
@@ -31,14 +36,18 @@ struct GenPlan {
 };
 
 using ColFn = cudaError_t (*)(const ColArgs&, cudaStream_t);
+using ColTmaFn = cudaError_t (*)(const ColArgs&, const CUtensorMap&, cudaStream_t);
 using RowFn = cudaError_t (*)(const RowArgs&, cudaStream_t);
 
 // Compile-time specialised kernels for one transform length.
 struct LenEntry {
     int L;
-    int col_E, col_W;    // column kernel: elements per thread, columns per CTA
-    int row_E, row_rows; // row kernels (0 when not instantiated for this L)
+    int col_E, col_W;  // plain column kernel: elements per thread, columns per CTA
     ColFn col_fwd, col_inv;
+    int tma_E, tma_W;  // TMA-fed persistent column kernel (tma_W = 0: none)
+    ColTmaFn tma_fwd, tma_inv;
+    int row_E, row_rows;  // row kernels (row_E = 0: none)
+    bool row_warp;        // rows resident in warps (shuffle unpack) or staged in shared memory
     RowFn r2c, c2r;
 };
 

@@ -4,11 +4,14 @@
 #pragma once
 #include "kernels.cuh"
 
-#define FFT3D_ENTRY_COLROW(L, CE, CW, RE, RR)                                                    \
-    fft3d::LenEntry{L, CE, CW, RE, RR, &fft3d::launch_col<L, CE, CW, -1>,                       \
-                    &fft3d::launch_col<L, CE, CW, 1>, &fft3d::launch_row<L, RE, RR, -1>,          \
-                    &fft3d::launch_row<L, RE, RR, 1>}
-
-#define FFT3D_ENTRY_COL(L, CE, CW)                                                               \
-    fft3d::LenEntry{L, CE, CW, 0, 0, &fft3d::launch_col<L, CE, CW, -1>,                         \
-                    &fft3d::launch_col<L, CE, CW, 1>, nullptr, nullptr}
+// plain column kernel: E elements per thread, W columns per CTA
+#define FFT3D_COL(L, E, W) E, W, &fft3d::launch_col<L, E, W, -1>, &fft3d::launch_col<L, E, W, 1>
+#define FFT3D_NO_TMA 0, 0, nullptr, nullptr
+// TMA-fed persistent column kernel: E, W, ring stages, L2 prefetch distance
+#define FFT3D_TMA(L, E, W, ST, PF) \
+    E, W, &fft3d::launch_col_tma<L, E, W, ST, -1, PF>, &fft3d::launch_col_tma<L, E, W, ST, 1, PF>
+// warp-resident rows (T = L/E <= 32), ROWS rows per CTA
+#define FFT3D_ROWW(L, E, R) E, R, true, &fft3d::launch_row_warp<L, E, R, -1>, &fft3d::launch_row_warp<L, E, R, 1>
+// shared-memory staged rows
+#define FFT3D_ROWS(L, E, R) E, R, false, &fft3d::launch_row<L, E, R, -1>, &fft3d::launch_row<L, E, R, 1>
+#define FFT3D_NO_ROW 0, 0, false, nullptr, nullptr

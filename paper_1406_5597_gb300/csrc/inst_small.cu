@@ -5,11 +5,11 @@ namespace fft3d {
 const LenEntry* entries_small(int* n)
 {
     static const LenEntry e[] = {
-        FFT3D_ENTRY_COLROW(8, 8, 256, 8, 128),
-        FFT3D_ENTRY_COLROW(16, 16, 256, 16, 128),
-        FFT3D_ENTRY_COLROW(32, 8, 64, 8, 64),
-        FFT3D_ENTRY_COLROW(64, 8, 32, 8, 32),
-        FFT3D_ENTRY_COLROW(128, 8, 32, 8, 16),
+        {8, FFT3D_COL(8, 8, 256), FFT3D_NO_TMA, FFT3D_ROWW(8, 8, 64)},
+        {16, FFT3D_COL(16, 16, 256), FFT3D_NO_TMA, FFT3D_ROWW(16, 16, 64)},
+        {32, FFT3D_COL(32, 8, 64), FFT3D_NO_TMA, FFT3D_ROWW(32, 8, 16)},
+        {64, FFT3D_COL(64, 8, 32), FFT3D_NO_TMA, FFT3D_ROWW(64, 8, 8)},
+        {128, FFT3D_COL(128, 8, 32), FFT3D_NO_TMA, FFT3D_ROWW(128, 8, 4)},
     };
     *n = (int)(sizeof(e) / sizeof(e[0]));
     return e;

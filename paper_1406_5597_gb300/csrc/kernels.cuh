@@ -23,6 +23,7 @@
 
 #include "args.h"
 #include "stockham.cuh"
+#include "tma.cuh"
 
 namespace fft3d {
 
@@ -168,6 +169,293 @@ __global__ void __launch_bounds__((L / E) * ROWS) row_c2r_kernel(RowArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// Warp-resident row kernels (T = L/E <= 32 threads per row, rows packed into
+// warps).  Each thread reads its positions t + T*m straight from global memory
+// (adjacent lanes, adjacent addresses), so only the Stockham exchanges touch
+// shared memory.  The Hermitian unpack/pack needs, next to bin k = t + T*m,
+// bin L-k: for t > 0 that is position (T-t) + T*(E-1-m), held by lane T-t of
+// the same row in register E-1-m; for t = 0 it is T*(E-m), the thread's own
+// register (E-m) mod E.  One warp shuffle per value replaces a shared-memory
+// round trip.  The unpack twiddle W_{2L}^k is formed as W_{2L}^t * W_{2L}^{T m}.
+// ---------------------------------------------------------------------------
+template <int T>
+__device__ __forceinline__ int row_partner_lane(int t)
+{
+    const int lane = threadIdx.x + threadIdx.y * T;  // lane within the warp (block x = T)
+    return (lane & 31) - t + ((T - t) & (T - 1));
+}
+
+template <int L, int E, int ROWS>
+__global__ void __launch_bounds__((L / E) * ROWS) row_r2c_warp_kernel(RowArgs a)
+{
+    extern __shared__ float2 sm[];
+    constexpr int T = L / E;
+    static_assert(T <= 32 && (32 % T) == 0, "rows must pack into warps");
+    constexpr int H = L + 1;
+    constexpr int RS = RowLayout<L>::stride;
+    const int t = threadIdx.x, r = threadIdx.y;
+    const long long row = (long long)blockIdx.x * ROWS + r;
+    const bool active = row < a.rows;
+    const float2* in = reinterpret_cast<const float2*>(a.in) + row * L;
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = active ? __ldg(&in[t + T * m]) : make_float2(0.f, 0.f);
+    RowExchange<true> ex{sm + r * RS};
+    fft_group<L, E, -1>(v, t, a.tw, ex);
+    const int partner = row_partner_lane<T>(t);
+    const float2 wt = __ldg(&a.twpack[t]);
+    float2* out = reinterpret_cast<float2*>(a.out) + row * H;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        float2 g;
+        g.x = __shfl_sync(0xffffffffu, v[E - 1 - m].x, partner);
+        g.y = __shfl_sync(0xffffffffu, v[E - 1 - m].y, partner);
+        const float2 zk = v[m];
+        const float2 zc = cconj(t == 0 ? v[(E - m) % E] : g);
+        const float2 s = cadd(zk, zc);
+        const float2 d = csub(zk, zc);
+        const float2 w = (m == 0) ? wt : cmul(wt, __ldg(&a.twpack[T * m]));
+        const float2 wd = cmul(d, w);  // X = s/2 - (i/2) W^k d
+        if (active) out[t + T * m] = make_float2(0.5f * (s.x + wd.y), 0.5f * (s.y - wd.x));
+    }
+    if (active && t == 0) out[L] = make_float2(v[0].x - v[0].y, 0.f);
+}
+
+template <int L, int E, int ROWS>
+__global__ void __launch_bounds__((L / E) * ROWS) row_c2r_warp_kernel(RowArgs a)
+{
+    extern __shared__ float2 sm[];
+    constexpr int T = L / E;
+    static_assert(T <= 32 && (32 % T) == 0, "rows must pack into warps");
+    constexpr int H = L + 1;
+    constexpr int RS = RowLayout<L>::stride;
+    const int t = threadIdx.x, r = threadIdx.y;
+    const long long row = (long long)blockIdx.x * ROWS + r;
+    const bool active = row < a.rows;
+    const float2* in = reinterpret_cast<const float2*>(a.in) + row * H;
+    float2 x[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[m] = active ? __ldg(&in[t + T * m]) : make_float2(0.f, 0.f);
+    const float2 nyq = (active && t == 0) ? __ldg(&in[L]) : make_float2(0.f, 0.f);
+    const int partner = row_partner_lane<T>(t);
+    const float2 wt = __ldg(&a.twpack[t]);
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        float2 g;
+        g.x = __shfl_sync(0xffffffffu, x[E - 1 - m].x, partner);
+        g.y = __shfl_sync(0xffffffffu, x[E - 1 - m].y, partner);
+        float2 xk = x[m];
+        float2 xc;
+        if (t == 0) {
+            // bin L - T*m: the Nyquist bin for m = 0, else own register E - m
+            xc = cconj(m == 0 ? nyq : x[(E - m) % E]);
+            if (m == 0) {  // Im of the DC and Nyquist bins is not part of a real row's spectrum
+                xk.y = 0.f;
+                xc.y = 0.f;
+            }
+        } else {
+            xc = cconj(g);
+        }
+        const float2 s = cadd(xk, xc);
+        const float2 d = csub(xk, xc);
+        const float2 w = (m == 0) ? wt : cmul(wt, __ldg(&a.twpack[T * m]));
+        const float2 wd = cmulc(d, w);  // Z = s + i W^{-k} d
+        v[m] = make_float2(s.x - wd.y, s.y + wd.x);
+    }
+    RowExchange<true> ex{sm + r * RS};
+    fft_group<L, E, +1>(v, t, a.tw, ex);
+    float2* out = reinterpret_cast<float2*>(a.out) + row * L;
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) out[t + T * m] = v[m];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent, pipelined column kernel.  Each CTA walks tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...; the elements of the tile STAGES-1 steps ahead
+// are copied global -> shared with cp.async while the current tile is
+// transformed, so loads, butterflies and stores of different tiles overlap.
+// A thread copies exactly the elements it later reads (positions t + T*m of
+// its column), so a stage buffer needs no barrier: cp.async.wait_group on the
+// thread's own copy groups is enough.  Only the Stockham exchange buffer is
+// shared between threads.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int L, int E, int DIR, int W, int STAGES>
+__global__ void __launch_bounds__(W*(L / E)) col_pipe_kernel(ColArgs a, long long ntiles)
+{
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int T = L / E;
+    const int c = threadIdx.x;
+    const int t = threadIdx.y;
+    const long long ctiles = (a.C + W - 1) / W;
+    float2* ex_buf = sm + (size_t)STAGES * L * W;
+
+    auto issue = [&](long long tile, int stage) {
+        if (tile < ntiles) {
+            const long long b = tile / ctiles;
+            const long long c0 = (tile - b * ctiles) * W;
+            if (c0 + c < a.C) {
+                const float2* src = a.data + b * a.Bs + c0 + c;
+                float2* dst = sm + (size_t)stage * L * W + c;
+#pragma unroll
+                for (int m = 0; m < E; ++m) cp_async8(dst + (t + T * m) * W, src + (long long)(t + T * m) * a.S);
+            }
+        }
+        cp_async_commit();  // one group per tile slot, possibly empty, keeps the counting uniform
+    };
+
+    long long tile = blockIdx.x;
+#pragma unroll
+    for (int s = 0; s < STAGES - 1; ++s) issue(tile + (long long)s * gridDim.x, s);
+    int stage = 0;
+    for (; tile < ntiles; tile += gridDim.x) {
+        issue(tile + (long long)(STAGES - 1) * gridDim.x, (stage + STAGES - 1) % STAGES);
+        cp_async_wait<STAGES - 1>();
+        const long long b = tile / ctiles;
+        const long long c0 = (tile - b * ctiles) * W;
+        const bool active = (c0 + c) < a.C;
+        const float2* buf = sm + (size_t)stage * L * W + c;
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = active ? buf[(t + T * m) * W] : make_float2(0.f, 0.f);
+        ColExchange exch{ex_buf, W, c};
+        fft_group<L, E, DIR>(v, t, a.tw, exch);
+        if (active) {
+            float2* dst = a.data + b * a.Bs + c0 + c;
+#pragma unroll
+            for (int m = 0; m < E; ++m) dst[(long long)(t + T * m) * a.S] = cscale(v[m], a.scale);
+        }
+        stage = (stage + 1) % STAGES;
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// TMA-fed persistent column kernel (the n0 pass).  The volume is seen as a 2D
+// FP32 tensor: inner extent 2*C floats (the flat (k1, k2) plane), outer extent
+// nb*L rows at a byte stride of 8*S.  A tile (W columns x L rows) arrives with
+// L/256 bulk tensor copies into one slot of a STAGES-deep shared-memory ring;
+// one elected thread keeps STAGES-1 tiles in flight, completion is counted on
+// the slot's mbarrier (transaction bytes), so the copies hold no registers and
+// no thread issue slots.  After the threads have read their values from the
+// slot, the slot doubles as the Stockham exchange buffer; results go straight
+// from registers to global memory.  Every mbarrier wait is bounded: a wait
+// that gives up sets kStatusTimeout in the device status word, and the CTA
+// drains its outstanding copies (again bounded) before returning.
+// Requirements (checked by the host): 8*S and the base address 16-byte
+// aligned, Bs == L*S, W*8 a multiple of 16.
+// ---------------------------------------------------------------------------
+constexpr unsigned kMbarMaxTries = 1u << 20;
+
+template <int L, int E, int DIR, int W, int STAGES, int PF = 0>
+__global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constant__ CUtensorMap tmap, ColArgs a,
+                                                           long long ntiles)
+{
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    constexpr int T = L / E;
+    constexpr int BOXR = L < 256 ? L : 256;
+    constexpr int NBOX = L / BOXR;
+    static_assert(L % BOXR == 0, "tile rows must split into boxes of <= 256 rows");
+    constexpr unsigned TILE_BYTES = (unsigned)L * W * sizeof(float2);
+    float2* ring = reinterpret_cast<float2*>(smraw);
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smraw + (size_t)STAGES * TILE_BYTES);
+    const int c = threadIdx.x;
+    const int t = threadIdx.y;
+    const bool leader = (c == 0 && t == 0);
+    const long long ctiles = (a.C + W - 1) / W;
+    int uses[STAGES];  // leader: loads issued per slot (parity bookkeeping for the drain)
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) uses[s] = 0;
+
+    if (leader) {
+        prefetch_tensormap(&tmap);
+#pragma unroll
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](long long tile, int s) {
+        if (tile >= ntiles) return;
+        const long long b = tile / ctiles;
+        const int x = (int)(2 * (tile - b * ctiles) * W);
+        mbar_arrive_expect_tx(&bars[s], TILE_BYTES);
+#pragma unroll
+        for (int k = 0; k < NBOX; ++k)
+            tma_load_2d(ring + (size_t)s * L * W + (size_t)k * BOXR * W, &tmap, x, (int)(b * L + k * BOXR), &bars[s]);
+        ++uses[s];
+        if constexpr (PF > 0) {  // warm L2 with the tile PF ring-lengths further on
+            const long long pt = tile + (long long)PF * gridDim.x;
+            if (pt < ntiles) {
+                const long long pb = pt / ctiles;
+                const int px = (int)(2 * (pt - pb * ctiles) * W);
+#pragma unroll
+                for (int k = 0; k < NBOX; ++k) tma_prefetch_l2_2d(&tmap, px, (int)(pb * L + k * BOXR));
+            }
+        }
+    };
+
+    if (leader) {
+#pragma unroll
+        for (int s = 0; s < STAGES - 1; ++s) issue(blockIdx.x + (long long)s * gridDim.x, s);
+    }
+    int stage = 0;
+    unsigned phase = 0;
+    int consumed[STAGES];
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) consumed[s] = 0;
+    bool failed = false;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const bool ok = mbar_wait_bounded(&bars[stage], phase, kMbarMaxTries);
+        if (!__syncthreads_and(ok)) {
+            failed = true;
+            break;
+        }
+        ++consumed[stage];
+        // the slot consumed in the previous iteration is free again: refill it
+        if (leader) issue(tile + (long long)(STAGES - 1) * gridDim.x, (stage + STAGES - 1) % STAGES);
+        const long long b = tile / ctiles;
+        const long long c0 = (tile - b * ctiles) * W;
+        const bool active = (c0 + c) < a.C;
+        float2* buf = ring + (size_t)stage * L * W;
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = buf[(t + T * m) * W + c];
+        __syncthreads();  // the slot now serves as the exchange buffer
+        ColExchange exch{buf, W, c};
+        fft_group<L, E, DIR>(v, t, a.tw, exch);
+        fence_proxy_async_smem();  // order this thread's shared accesses before the slot's next bulk copy
+        if (active) {
+            float2* dst = a.data + b * a.Bs + c0 + c;
+#pragma unroll
+            for (int m = 0; m < E; ++m) dst[(long long)(t + T * m) * a.S] = cscale(v[m], a.scale);
+        }
+        if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+        }
+    }
+    if (failed && leader) {
+        atomicOr(a.status, kStatusTimeout);
+        // drain: wait (bounded) for every copy issued but not consumed
+#pragma unroll
+        for (int s = 0; s < STAGES; ++s)
+            for (int u = consumed[s]; u < uses[s]; ++u) mbar_wait_bounded(&bars[s], (unsigned)(u & 1), kMbarMaxTries);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launchers (one instantiation per supported length).
 // ---------------------------------------------------------------------------
 struct ColShape {
@@ -231,6 +519,82 @@ inline cudaError_t launch_row(const RowArgs& a, cudaStream_t s)
         k<<<(unsigned)blocks, dim3(T, ROWS), smem, s>>>(a);
     }
     return cudaGetLastError();
+}
+
+template <int L, int E, int ROWS, int DIR>
+inline cudaError_t launch_row_warp(const RowArgs& a, cudaStream_t s)
+{
+    constexpr int T = L / E;
+    static_assert((T * ROWS) % 32 == 0, "the shuffles need whole warps");
+    const size_t smem = (num_stages(L, E) > 1) ? row_smem<L, E, ROWS>() : 0;
+    const long long blocks = (a.rows + ROWS - 1) / ROWS;
+    if (blocks <= 0) return cudaSuccess;
+    auto k = (DIR < 0) ? row_r2c_warp_kernel<L, E, ROWS> : row_c2r_warp_kernel<L, E, ROWS>;
+    static bool attr_set = false;
+    if (smem > 48 * 1024 && !attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k<<<(unsigned)blocks, dim3(T, ROWS), smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int L, int E, int W, int STAGES, int DIR>
+inline cudaError_t launch_col_pipe(const ColArgs& a, cudaStream_t s)
+{
+    constexpr int T = L / E;
+    const size_t smem = (size_t)(STAGES + 1) * L * W * sizeof(float2);
+    auto k = col_pipe_kernel<L, E, DIR, W, STAGES>;
+    static int grid_per_sm = 0;  // resident CTAs per SM, queried once per instantiation
+    static int sms = 0;
+    if (grid_per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&grid_per_sm, k, W * T, smem);
+        if (e != cudaSuccess) return e;
+        if (grid_per_sm < 1) return cudaErrorInvalidConfiguration;
+    }
+    const long long ntiles = a.nb * ((a.C + W - 1) / W);
+    if (ntiles <= 0) return cudaSuccess;
+    long long grid = (long long)grid_per_sm * sms;
+    if (grid > ntiles) grid = ntiles;
+    k<<<(unsigned)grid, dim3(W, T), smem, s>>>(a, ntiles);
+    return cudaGetLastError();
+}
+
+template <int L, int E, int W, int STAGES, int DIR, int PF = 0>
+inline cudaError_t launch_col_tma(const ColArgs& a, const CUtensorMap& map, cudaStream_t s)
+{
+    constexpr int T = L / E;
+    const size_t smem = (size_t)STAGES * L * W * sizeof(float2) + STAGES * sizeof(unsigned long long);
+    auto k = col_tma_kernel<L, E, DIR, W, STAGES, PF>;
+    static int per_sm = 0;
+    static int sms = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, W * T, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    }
+    const long long ntiles = a.nb * ((a.C + W - 1) / W);
+    if (ntiles <= 0) return cudaSuccess;
+    long long grid = (long long)per_sm * sms;
+    if (grid > ntiles) grid = ntiles;
+    k<<<(unsigned)grid, dim3(W, T), smem, s>>>(map, a, ntiles);
+    return cudaGetLastError();
+}
+
+inline cudaError_t col_tensor_map(CUtensorMap* map, const ColArgs& a, int L, int W)
+{
+    return col_tensor_map_host(map, a, L, W);
 }
 
 }  // namespace fft3d

@@ -86,6 +86,56 @@ struct RowExchange {
     }
 };
 
+// Twiddle inputs 1..R-1 of a radix-R butterfly by W^{k*base} (table units).
+// Only the powers 1, 2, 4 (and 8) are read from the FP32 table; the others
+// are products of two or three of them (each product adds one FP32 rounding).
+template <int R, int DIR>
+__device__ __forceinline__ void twiddle_inputs(float2* a, const float2* __restrict__ tw, int base)
+{
+    const float2 w1 = __ldg(&tw[base]);
+    if constexpr (R == 2) {
+        a[1] = twiddle<DIR>(a[1], w1);
+    } else if constexpr (R == 3) {
+        a[1] = twiddle<DIR>(a[1], w1);
+        a[2] = twiddle<DIR>(a[2], __ldg(&tw[2 * base]));
+    } else if constexpr (R == 4) {
+        const float2 w2 = __ldg(&tw[2 * base]);
+        a[1] = twiddle<DIR>(a[1], w1);
+        a[2] = twiddle<DIR>(a[2], w2);
+        a[3] = twiddle<DIR>(a[3], cmul(w1, w2));
+    } else if constexpr (R == 5) {
+        const float2 w2 = __ldg(&tw[2 * base]);
+        const float2 w4 = __ldg(&tw[4 * base]);
+        a[1] = twiddle<DIR>(a[1], w1);
+        a[2] = twiddle<DIR>(a[2], w2);
+        a[3] = twiddle<DIR>(a[3], cmul(w1, w2));
+        a[4] = twiddle<DIR>(a[4], w4);
+    } else if constexpr (R == 8 || R == 16) {
+        const float2 w2 = __ldg(&tw[2 * base]);
+        const float2 w4 = __ldg(&tw[4 * base]);
+        const float2 w3 = cmul(w1, w2);
+        a[1] = twiddle<DIR>(a[1], w1);
+        a[2] = twiddle<DIR>(a[2], w2);
+        a[3] = twiddle<DIR>(a[3], w3);
+        a[4] = twiddle<DIR>(a[4], w4);
+        a[5] = twiddle<DIR>(a[5], cmul(w1, w4));
+        a[6] = twiddle<DIR>(a[6], cmul(w2, w4));
+        a[7] = twiddle<DIR>(a[7], cmul(w3, w4));
+        if constexpr (R == 16) {
+            const float2 w8 = __ldg(&tw[8 * base]);
+            const float2 w12 = cmul(w4, w8);
+            a[8] = twiddle<DIR>(a[8], w8);
+            a[9] = twiddle<DIR>(a[9], cmul(w1, w8));
+            a[10] = twiddle<DIR>(a[10], cmul(w2, w8));
+            a[11] = twiddle<DIR>(a[11], cmul(w3, w8));
+            a[12] = twiddle<DIR>(a[12], w12);
+            a[13] = twiddle<DIR>(a[13], cmul(w1, w12));
+            a[14] = twiddle<DIR>(a[14], cmul(w2, w12));
+            a[15] = twiddle<DIR>(a[15], cmul(w3, w12));
+        }
+    }
+}
+
 template <int L, int E, int DIR, int S>
 struct Stage {
     template <class Ex>
@@ -107,8 +157,7 @@ struct Stage {
             const int jm = j % Ns;
             if constexpr (Ns > 1) {
                 constexpr int step = L / (Ns * R);
-#pragma unroll
-                for (int k = 1; k < R; ++k) a[k] = twiddle<DIR>(a[k], __ldg(&tw[k * jm * step]));
+                twiddle_inputs<R, DIR>(a, tw, jm * step);
             }
             Dft<R, DIR>::run(a);
             if constexpr (last) {

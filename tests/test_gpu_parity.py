@@ -121,6 +121,10 @@ SHAPES = [
     (48, 80, 96), (96, 96, 96), (160, 32, 160), (192, 48, 64), (64, 64, 192),
     (6, 10, 16), (15, 12, 10), (30, 20, 24), (2, 2, 2), (1, 1, 2), (1, 8, 16), (4, 1, 8), (5, 3, 2),
     (1536, 2, 4), (2048, 2, 4), (2, 2048, 4), (4, 4, 2048), (2, 3, 4096), (1024, 8, 8), (8, 1024, 8),
+    # n0 pass through the TMA kernel: ragged last column tile (OOB fill), P odd falls back
+    (512, 6, 10), (512, 5, 6), (256, 3, 4), (256, 40, 60), (1024, 6, 12),
+    # warp-resident rows at n2 = 1024, shared-memory rows at n2 = 2048
+    (8, 6, 1024), (3, 2, 2048),
 ]
 
 
@@ -143,6 +147,18 @@ def test_generic_kernels_forced(cuda_lib, shape):
     assert rel_l2(gpu_r2c(cuda_lib, x32, flags=f), oracle.r2c3d(x32.astype(np.float64))) <= TOL
     Y = random_half_spectrum((n0, n1, n2 // 2 + 1), seed=31)
     assert rel_l2(gpu_c2r(cuda_lib, Y, n2, flags=f), oracle.c2r3d(Y.astype(np.complex128), n2)) <= TOL
+
+
+def test_batched_tma_column_pass(cuda_lib):
+    shape = (3, 256, 8, 12)
+    x32 = synth.uniform_field(shape, seed=39).astype(np.float32)
+    X = gpu_r2c(cuda_lib, x32)
+    for b in range(3):
+        assert rel_l2(X[b], oracle.r2c3d(x32[b].astype(np.float64))) <= TOL
+    Y = random_half_spectrum((3 * 256, 8, 7), seed=40).reshape(3, 256, 8, 7)
+    y = gpu_c2r(cuda_lib, Y, 12)
+    for b in range(3):
+        assert rel_l2(y[b], oracle.c2r3d(Y[b].astype(np.complex128), 12)) <= TOL
 
 
 def test_batch_entries_do_not_bleed(cuda_lib):
