@@ -301,7 +301,8 @@ def main():
         variants = {}
         for name, flags in (("explicit_transpose", fft3d.FFT3D_FLAG_EXPLICIT_TRANSPOSE),
                             ("explicit_transpose_back", fft3d.FFT3D_FLAG_EXPLICIT_TRANSPOSE
-                             | fft3d.FFT3D_FLAG_TRANSPOSE_BACK)):
+                             | fft3d.FFT3D_FLAG_TRANSPOSE_BACK),
+                            ("fused_plane", fft3d.FFT3D_FLAG_FUSED_PLANE)):
             vp = fft3d.Plan(n, n, n, flags=flags)
 
             def vstep(vp=vp):

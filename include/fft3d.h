@@ -71,8 +71,17 @@ typedef enum {
 /* Plan flags for fft3d_plan_variant. */
 #define FFT3D_FLAG_EXPLICIT_TRANSPOSE 0x1 /* comparator: materialise the n0<->n1 transpose (Sec. 2.1, step 2) */
 #define FFT3D_FLAG_TRANSPOSE_BACK 0x2     /* with EXPLICIT_TRANSPOSE: transpose back to n0 x n1 x H */
-#define FFT3D_FLAG_THREE_PASS 0x4         /* force separate n2-row, n1-column and n0-column passes */
+#define FFT3D_FLAG_THREE_PASS 0x4         /* force separate n2-row, n1-column and n0-column passes (default) */
 #define FFT3D_FLAG_GENERIC 0x8            /* force the runtime-length kernels (testing) */
+#define FFT3D_FLAG_FUSED_PLANE 0x20       /* fuse the n2-row and n1-column passes into one persistent
+                                             kernel that keeps each plane in L2 between its halves
+                                             (DRAM traffic of two passes; shapes with an instantiated
+                                             fused kernel only, else ignored) */
+#define FFT3D_FLAG_TEST_SKIP_ARRIVAL 0x10 /* testing only (with FUSED_PLANE): in the fused plane kernel the producers of
+                                             plane 0 never report, so its consumers' bounded waits give
+                                             up after about a millisecond; the call's output is then
+                                             undefined and fft3d_query_device_status returns
+                                             FFT3D_ERR_TIMEOUT */
 
 /*
  * Create a plan for batch transforms of size n0 x n1 x n2 (Sec. 2).
@@ -153,13 +162,33 @@ int fft3d_set_profiling(fft3d_handle plan, int enable);
 int fft3d_profile_read(fft3d_handle plan, double* ms, int* count, int n);
 
 /* Static name of pass id i ("row_r2c", "col_n1_fwd", "col_n0_fwd",
- * "col_n0_inv", "col_n1_inv", "row_c2r", "swap01"); NULL past the last id. */
+ * "col_n0_inv", "col_n1_inv", "row_c2r", "swap01", "plane_fwd", "plane_inv");
+ * NULL past the last id. */
 const char* fft3d_pass_name(int pass);
 
 /* Algorithmic bytes one launch of pass id i moves with this plan: one read
  * plus one write of the data it transforms (4 bytes per real and 8 per complex
  * value).  Returns 0 for an unknown id. */
 double fft3d_pass_bytes(fft3d_handle plan, int pass);
+
+/*
+ * FP64 spectral diagnostics of a half spectrum (device-side checks of a
+ * transform, and the energy spectrum of a pseudo-spectral solver, Sec. 1).
+ * spec:   batch*n0*n1*H float2 (device), read only, laid out as fft3d_r2c
+ *         writes it for a plan without EXPLICIT_TRANSPOSE.
+ * total:  batch doubles (device) or NULL: sum over the half spectrum of
+ *         c_k2 |X|^2 (c_k2 = 1 at k2 = 0 and k2 = n2/2, else 2), which equals
+ *         n0*n1*n2 * sum_j x_j^2 when spec = r2c(x) (Parseval).
+ * shells: batch*nbins doubles (device) or NULL: the same sum per integer
+ *         shell b = floor(|k| + 1/2) (shell 0 holds only k = 0; shell b >= 1
+ *         is (2b-1)^2 <= 4|k|^2 < (2b+1)^2), |k_a| = min(j_a, n_a - j_a),
+ *         decided in integers; bins of shell >= nbins are left out.
+ * 1 <= nbins <= 8192.  |X|^2 in FP32, sums in FP64, block partials summed in
+ * a fixed order (deterministic).  Uses plan-owned scratch (allocated at plan
+ * time for nbins up to the largest shell of the shape; a larger nbins grows
+ * it, which synchronises the device).  Asynchronous on stream otherwise.
+ */
+int fft3d_energy(fft3d_handle plan, const void* spec, double* total, double* shells, int nbins, void* stream);
 
 #ifdef __cplusplus
 }

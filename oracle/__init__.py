@@ -190,9 +190,10 @@ def half_energy(X: np.ndarray, n2: int) -> float:
 
 
 def shell_index(n0: int, n1: int, n2: int) -> np.ndarray:
-    """Integer shell b of every half-spectrum bin: the b with
-    (2b-1)^2 <= 4|k|^2 < (2b+1)^2, |k_a| = min(j_a, n_a - j_a).  Integer only,
-    so no rounding decides a bin."""
+    """Integer shell b = floor(|k| + 1/2) of every half-spectrum bin, with
+    |k_a| = min(j_a, n_a - j_a): b = 0 holds only k = 0, and for b >= 1 the
+    shell is (2b-1)^2 <= 4|k|^2 < (2b+1)^2.  Decided in integers, so no
+    rounding picks a bin."""
     H = n2 // 2 + 1
     a0 = np.minimum(np.arange(n0), n0 - np.arange(n0)).astype(np.int64)
     a1 = np.minimum(np.arange(n1), n1 - np.arange(n1)).astype(np.int64)
@@ -200,7 +201,7 @@ def shell_index(n0: int, n1: int, n2: int) -> np.ndarray:
     kk4 = 4 * (a0[:, None, None] ** 2 + a1[None, :, None] ** 2 + a2[None, None, :] ** 2)
     b = np.floor((np.sqrt(kk4.astype(np.float64)) + 1.0) / 2.0).astype(np.int64)
     # integer correction of any floating-point slip
-    b = np.where((2 * b - 1) ** 2 > kk4, b - 1, b)
+    b = np.where((b > 0) & ((2 * b - 1) ** 2 > kk4), b - 1, b)
     b = np.where((2 * b + 1) ** 2 <= kk4, b + 1, b)
     return b
 

@@ -37,6 +37,8 @@ FFT3D_FLAG_EXPLICIT_TRANSPOSE = 0x1
 FFT3D_FLAG_TRANSPOSE_BACK = 0x2
 FFT3D_FLAG_THREE_PASS = 0x4
 FFT3D_FLAG_GENERIC = 0x8
+FFT3D_FLAG_TEST_SKIP_ARRIVAL = 0x10
+FFT3D_FLAG_FUSED_PLANE = 0x20
 
 _lib = None
 _lock = threading.Lock()
@@ -60,6 +62,7 @@ _SIGS = {
     "fft3d_profile_read": ([_P, _P, _P, _I], _I),
     "fft3d_pass_name": ([_I], ctypes.c_char_p),
     "fft3d_pass_bytes": ([_P, _I], ctypes.c_double),
+    "fft3d_energy": ([_P, _P, _P, _P, _I, _P], _I),
 }
 
 
@@ -190,6 +193,10 @@ def fft3d_pass_bytes(plan, pass_id):
     return load().fft3d_pass_bytes(_v(plan), pass_id)
 
 
+def fft3d_energy(plan, spec_ptr, total_ptr, shells_ptr, nbins, stream=0):
+    return load().fft3d_energy(_v(plan), _v(spec_ptr), _v(total_ptr), _v(shells_ptr), nbins, _v(stream))
+
+
 def error_string(status: int) -> str:
     try:
         return fft3d_error_string(status)
@@ -232,6 +239,17 @@ class Plan:
         st = fft3d_c2r(self.handle, in_ptr, out_ptr, stream)
         if st != FFT3D_OK:
             raise Fft3dError(st, "fft3d_c2r")
+
+    def energy(self, spec, nbins):
+        """(total, shells) FP64 CUDA tensors of a complex64 CUDA spectrum tensor."""
+        import torch
+        total = torch.empty(self.batch, dtype=torch.float64, device=spec.device)
+        shells = torch.empty((self.batch, nbins), dtype=torch.float64, device=spec.device)
+        st = fft3d_energy(self.handle, spec.data_ptr(), total.data_ptr(), shells.data_ptr(), nbins,
+                          _stream_ptr(None))
+        if st != FFT3D_OK:
+            raise Fft3dError(st, "fft3d_energy")
+        return total, shells
 
     def close(self):
         if self.handle:

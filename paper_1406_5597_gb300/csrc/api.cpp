@@ -18,7 +18,9 @@
 #include <vector>
 
 #include "args.h"
+#include "energy.h"
 #include "fft3d.h"
+#include "plane.h"
 #include "tma_host.h"
 
 namespace fft3d {
@@ -130,9 +132,9 @@ struct Axis {
 }  // namespace
 
 enum PassId { PASS_ROW_R2C = 0, PASS_N1_FWD, PASS_N0_FWD, PASS_N0_INV, PASS_N1_INV, PASS_ROW_C2R, PASS_SWAP01,
-              PASS_COUNT };
-const char* const kPassNames[PASS_COUNT] = {"row_r2c", "col_n1_fwd", "col_n0_fwd", "col_n0_inv",
-                                            "col_n1_inv", "row_c2r", "swap01"};
+              PASS_PLANE_FWD, PASS_PLANE_INV, PASS_COUNT };
+const char* const kPassNames[PASS_COUNT] = {"row_r2c",    "col_n1_fwd", "col_n0_fwd", "col_n0_inv", "col_n1_inv",
+                                            "row_c2r",    "swap01",     "plane_fwd",  "plane_inv"};
 
 struct ProfRecord {
     int pass;
@@ -146,6 +148,12 @@ struct fft3d_plan_s {
     Axis ax0, ax1, ax2;  // ax2: length n2/2 (row transform)
     float2* d_twpack = nullptr;
     int* d_status = nullptr;
+    const PlaneEntry* plane = nullptr;  // fused n2+n1 kernel, when one fits this shape
+    int* d_counters = nullptr;          // per-plane completion counters + work ticket of the fused kernel
+    float2* d_ring = nullptr;           // inverse fused kernel: L2-resident ring of n1-transformed planes
+    int ring_planes = 0;
+    double* d_energy = nullptr;         // scratch of fft3d_energy (block partials)
+    size_t energy_doubles = 0;
     void* workspace = nullptr;
     std::string desc;
     bool profiling = false;
@@ -181,6 +189,9 @@ void free_plan(fft3d_plan_s* p)
     cudaFree(p->ax2.d_tw);
     cudaFree(p->d_twpack);
     cudaFree(p->d_status);
+    cudaFree(p->d_counters);
+    cudaFree(p->d_ring);
+    cudaFree(p->d_energy);
     delete p;
 }
 
@@ -278,6 +289,32 @@ std::string axis_desc(const fft3d_plan_s* p, const Axis& a, bool row)
     return b;
 }
 
+// The fused plane pass (rows + n1 columns of every plane in one launch).
+cudaError_t run_plane(fft3d_plan_s* p, int dir, const void* in, void* out, cudaStream_t s)
+{
+    ProfScope ps(p, dir < 0 ? PASS_PLANE_FWD : PASS_PLANE_INV, s);
+    const long long planes = (long long)p->batch * p->n0;
+    cudaError_t e = cudaMemsetAsync(p->d_counters, 0, (size_t)(((planes + 1) & ~1LL) + 2) * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    PlaneArgs a;
+    a.in = in;
+    a.out = out;
+    a.planes = planes;
+    a.H = p->H;
+    a.tw_row = p->ax2.d_tw;
+    a.twpack = p->d_twpack;
+    a.tw_col = p->ax1.d_tw;
+    a.counters = p->d_counters;
+    a.ring = p->d_ring;
+    a.ring_planes = p->ring_planes;
+    a.status = p->d_status;
+    a.lag = 2;
+    const bool test_skip = p->flags & FFT3D_FLAG_TEST_SKIP_ARRIVAL;
+    a.wait_limit = test_skip ? 4000u : 20000000u;  // ~1 ms in the test hook, seconds otherwise
+    a.skip_plane = test_skip ? 0 : -1;
+    return dir < 0 ? p->plane->fwd(a, s) : p->plane->inv(a, s);
+}
+
 cudaError_t run_swap(fft3d_plan_s* p, const float2* in, float2* out, long long a0, long long a1, cudaStream_t s)
 {
     ProfScope ps(p, PASS_SWAP01, s);
@@ -315,7 +352,7 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
 {
     if (n0 < 1 || n1 < 1 || n2 < 2 || batch < 1 || dtype < 0 || dtype > 2 ||
         (flags & ~(FFT3D_FLAG_EXPLICIT_TRANSPOSE | FFT3D_FLAG_TRANSPOSE_BACK | FFT3D_FLAG_THREE_PASS |
-                   FFT3D_FLAG_GENERIC)) ||
+                   FFT3D_FLAG_GENERIC | FFT3D_FLAG_TEST_SKIP_ARRIVAL | FFT3D_FLAG_FUSED_PLANE)) ||
         ((flags & FFT3D_FLAG_TRANSPOSE_BACK) && !(flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE))) {
         fail(FFT3D_ERR_INVALID_ARG);
         return nullptr;
@@ -371,8 +408,56 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
         fail(FFT3D_ERR_ALLOC);
         return nullptr;
     }
+    if ((flags & FFT3D_FLAG_FUSED_PLANE) &&
+        !(flags & (FFT3D_FLAG_THREE_PASS | FFT3D_FLAG_GENERIC | FFT3D_FLAG_EXPLICIT_TRANSPOSE))) {
+        int np = 0;
+        const PlaneEntry* pe = plane_entries(&np);
+        for (int i = 0; i < np; ++i)
+            if (pe[i].LR == n2 / 2 && pe[i].LC == n1) p->plane = &pe[i];
+        // per-plane counters, then an 8-byte work ticket (kept 8-byte aligned)
+        const size_t ncount = (((size_t)batch * n0 + 1) & ~(size_t)1) + 2;
+        if (p->plane && cudaMalloc((void**)&p->d_counters, ncount * sizeof(int)) != cudaSuccess) {
+            free_plan(p);
+            fail(FFT3D_ERR_ALLOC);
+            return nullptr;
+        }
+        // Inverse ring: as many planes as can be in flight (bounded by the item
+        // lag the kernel derives, well under this) so the clobbered spectrum
+        // is never written back to DRAM.  At most 64 MiB.
+        if (p->plane) {
+            const size_t plane_bytes = (size_t)n1 * (n2 / 2 + 1) * sizeof(float2);
+            int rp = (int)((64u << 20) / plane_bytes);
+            if (rp > 32) rp = 32;
+            if (rp >= 16 && (long long)rp < (long long)batch * n0) {
+                if (cudaMalloc((void**)&p->d_ring, (size_t)rp * plane_bytes) != cudaSuccess) {
+                    free_plan(p);
+                    fail(FFT3D_ERR_ALLOC);
+                    return nullptr;
+                }
+                p->ring_planes = rp;
+            }
+        }
+    }
+    {
+        // energy scratch for nbins up to the largest shell of the shape
+        const double kmax = std::sqrt((double)(n0 / 2) * (n0 / 2) + (double)(n1 / 2) * (n1 / 2) +
+                                      (double)(n2 / 2) * (n2 / 2));
+        const int nb = (int)kmax + 2;
+        p->energy_doubles = energy_scratch_doubles(batch, (long long)n0 * n1, nb);
+        if (cudaMalloc((void**)&p->d_energy, p->energy_doubles * sizeof(double)) != cudaSuccess) {
+            free_plan(p);
+            fail(FFT3D_ERR_ALLOC);
+            return nullptr;
+        }
+    }
     std::string d = "rows[" + axis_desc(p, p->ax2, true) + "] n1[" + axis_desc(p, p->ax1, false) + "] n0[" +
                     axis_desc(p, p->ax0, false) + "]";
+    if (p->plane) {
+        char b[128];
+        std::snprintf(b, sizeof b, "plane[fused rows E=%d + n1 E=%d, %d threads]", p->plane->ER, p->plane->EC,
+                      p->plane->NT);
+        d = std::string(b) + " n0[" + axis_desc(p, p->ax0, false) + "]";
+    }
     if (flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE)
         d += (flags & FFT3D_FLAG_TRANSPOSE_BACK) ? " explicit-transpose+back" : " explicit-transpose";
     p->desc = d;
@@ -417,6 +502,7 @@ int fft3d_launches_per_call(fft3d_handle p, int dir)
 {
     if (!p) return fail(FFT3D_ERR_INVALID_ARG);
     (void)dir;
+    if (p->plane) return 1 + (p->n0 > 1);
     int n = 1 + (p->n1 > 1) + (p->n0 > 1);
     if (p->flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE) n += (p->flags & FFT3D_FLAG_TRANSPOSE_BACK) ? 2 : 1;
     return n;
@@ -447,6 +533,11 @@ int fft3d_r2c(fft3d_handle p, const float* in, void* out, void* stream)
     const long long H = p->H, n0 = p->n0, n1 = p->n1, B = p->batch;
     float2* o = (float2*)out;
     cudaError_t e;
+    if (!xpose && p->plane) {
+        if (run_plane(p, -1, in, o, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_col(p, p->ax0, -1, o, p->P, p->P, B, p->M, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        return FFT3D_OK;
+    }
     if (!xpose) {
         if ((e = run_row(p, -1, in, o, s)) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
         if ((e = run_col(p, p->ax1, -1, o, H, H, B * n0, n1 * H, s)) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
@@ -483,6 +574,11 @@ int fft3d_c2r(fft3d_handle p, void* in, float* out, void* stream)
     cudaStream_t s = (cudaStream_t)stream;
     const long long H = p->H, n0 = p->n0, n1 = p->n1, B = p->batch;
     float2* x = (float2*)in;
+    if (!xpose && p->plane) {
+        if (run_col(p, p->ax0, +1, x, p->P, p->P, B, p->M, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_plane(p, +1, x, out, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        return FFT3D_OK;
+    }
     if (!xpose) {
         if (run_col(p, p->ax0, +1, x, p->P, p->P, B, p->M, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
         if (run_col(p, p->ax1, +1, x, H, H, B * n0, n1 * H, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
@@ -503,6 +599,25 @@ int fft3d_c2r(fft3d_handle p, void* in, float* out, void* stream)
         if (run_col(p, p->ax1, +1, x, H, H, B * n0, n1 * H, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
         if (run_row(p, +1, x, out, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
     }
+    return FFT3D_OK;
+}
+
+int fft3d_energy(fft3d_handle p, const void* spec, double* total, double* shells, int nbins, void* stream)
+{
+    if (!p || !spec || nbins < 1 || nbins > 8192 || (!total && !shells)) return fail(FFT3D_ERR_INVALID_ARG);
+    if (((uintptr_t)spec & 15) || ((uintptr_t)total & 7) || ((uintptr_t)shells & 7)) return fail(FFT3D_ERR_MISALIGNED);
+    const size_t need = energy_scratch_doubles(p->batch, (long long)p->n0 * p->n1, nbins);
+    if (need > p->energy_doubles) {
+        cudaDeviceSynchronize();
+        cudaFree(p->d_energy);
+        p->d_energy = nullptr;
+        p->energy_doubles = 0;
+        if (cudaMalloc((void**)&p->d_energy, need * sizeof(double)) != cudaSuccess) return fail(FFT3D_ERR_ALLOC);
+        p->energy_doubles = need;
+    }
+    if (launch_energy(spec, p->n0, p->n1, p->n2, p->batch, nbins, p->d_energy, total, shells,
+                      (cudaStream_t)stream) != cudaSuccess)
+        return fail(FFT3D_ERR_CUDA);
     return FFT3D_OK;
 }
 
@@ -554,6 +669,8 @@ double fft3d_pass_bytes(fft3d_handle p, int pass)
     case PASS_N0_FWD:
     case PASS_N0_INV: return p->n0 > 1 ? 2.0 * cplx : 0.0;
     case PASS_SWAP01: return 2.0 * cplx;
+    case PASS_PLANE_FWD:
+    case PASS_PLANE_INV: return real + cplx;
     default: return 0.0;
     }
 }

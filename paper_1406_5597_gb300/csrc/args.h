@@ -53,6 +53,17 @@ struct LenEntry {
 
 const LenEntry* find_len(int L);
 
+struct PlaneArgs;
+using PlaneFn = cudaError_t (*)(const PlaneArgs&, cudaStream_t);
+
+// Fused plane kernel for one (n2/2, n1) pair.
+struct PlaneEntry {
+    int LR, LC;  // n2/2 and n1
+    int ER, EC, NT;
+    PlaneFn fwd, inv;
+};
+const PlaneEntry* plane_entries(int* n);
+
 // Generic kernels: dir = -1 forward, +1 inverse.
 cudaError_t generic_col(const ColArgs& a, const GenPlan& g, int dir, cudaStream_t s);
 cudaError_t generic_row(const RowArgs& a, const GenPlan& g, int dir, cudaStream_t s);

@@ -178,33 +178,30 @@ __global__ void __launch_bounds__((L / E) * ROWS) row_c2r_kernel(RowArgs a)
 // register (E-m) mod E.  One warp shuffle per value replaces a shared-memory
 // round trip.  The unpack twiddle W_{2L}^k is formed as W_{2L}^t * W_{2L}^{T m}.
 // ---------------------------------------------------------------------------
-template <int T>
-__device__ __forceinline__ int row_partner_lane(int t)
+template <bool CG>
+__device__ __forceinline__ float2 ld2(const float2* p)
 {
-    const int lane = threadIdx.x + threadIdx.y * T;  // lane within the warp (block x = T)
-    return (lane & 31) - t + ((T - t) & (T - 1));
+    if constexpr (CG) return __ldcg(p);  // L2 only: data another CTA wrote during this launch
+    else return __ldg(p);
 }
 
-template <int L, int E, int ROWS>
-__global__ void __launch_bounds__((L / E) * ROWS) row_r2c_warp_kernel(RowArgs a)
+// r2c of one row: in_row = packed row (L float2), out_row = H bins.  t in
+// [0, T), lane = this thread's lane in its warp; the T threads of a row are
+// consecutive lanes.  sm_row: RowLayout<L>::stride float2 of exchange space.
+template <int L, int E, bool CG>
+__device__ __forceinline__ void row_r2c_body(const float2* in_row, float2* out_row, bool active, int t, int lane,
+                                             float2* sm_row, const float2* __restrict__ tw,
+                                             const float2* __restrict__ twpack)
 {
-    extern __shared__ float2 sm[];
     constexpr int T = L / E;
     static_assert(T <= 32 && (32 % T) == 0, "rows must pack into warps");
-    constexpr int H = L + 1;
-    constexpr int RS = RowLayout<L>::stride;
-    const int t = threadIdx.x, r = threadIdx.y;
-    const long long row = (long long)blockIdx.x * ROWS + r;
-    const bool active = row < a.rows;
-    const float2* in = reinterpret_cast<const float2*>(a.in) + row * L;
     float2 v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = active ? __ldg(&in[t + T * m]) : make_float2(0.f, 0.f);
-    RowExchange<true> ex{sm + r * RS};
-    fft_group<L, E, -1>(v, t, a.tw, ex);
-    const int partner = row_partner_lane<T>(t);
-    const float2 wt = __ldg(&a.twpack[t]);
-    float2* out = reinterpret_cast<float2*>(a.out) + row * H;
+    for (int m = 0; m < E; ++m) v[m] = active ? ld2<CG>(&in_row[t + T * m]) : make_float2(0.f, 0.f);
+    RowExchange<true> ex{sm_row};
+    fft_group<L, E, -1>(v, t, tw, ex);
+    const int partner = lane - t + ((T - t) & (T - 1));
+    const float2 wt = __ldg(&twpack[t]);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         float2 g;
@@ -214,31 +211,27 @@ __global__ void __launch_bounds__((L / E) * ROWS) row_r2c_warp_kernel(RowArgs a)
         const float2 zc = cconj(t == 0 ? v[(E - m) % E] : g);
         const float2 s = cadd(zk, zc);
         const float2 d = csub(zk, zc);
-        const float2 w = (m == 0) ? wt : cmul(wt, __ldg(&a.twpack[T * m]));
+        const float2 w = (m == 0) ? wt : cmul(wt, __ldg(&twpack[T * m]));
         const float2 wd = cmul(d, w);  // X = s/2 - (i/2) W^k d
-        if (active) out[t + T * m] = make_float2(0.5f * (s.x + wd.y), 0.5f * (s.y - wd.x));
+        if (active) out_row[t + T * m] = make_float2(0.5f * (s.x + wd.y), 0.5f * (s.y - wd.x));
     }
-    if (active && t == 0) out[L] = make_float2(v[0].x - v[0].y, 0.f);
+    if (active && t == 0) out_row[L] = make_float2(v[0].x - v[0].y, 0.f);
 }
 
-template <int L, int E, int ROWS>
-__global__ void __launch_bounds__((L / E) * ROWS) row_c2r_warp_kernel(RowArgs a)
+// c2r of one row: in_row = H bins, out_row = packed real row (L float2).
+template <int L, int E, bool CG>
+__device__ __forceinline__ void row_c2r_body(const float2* in_row, float2* out_row, bool active, int t, int lane,
+                                             float2* sm_row, const float2* __restrict__ tw,
+                                             const float2* __restrict__ twpack)
 {
-    extern __shared__ float2 sm[];
     constexpr int T = L / E;
     static_assert(T <= 32 && (32 % T) == 0, "rows must pack into warps");
-    constexpr int H = L + 1;
-    constexpr int RS = RowLayout<L>::stride;
-    const int t = threadIdx.x, r = threadIdx.y;
-    const long long row = (long long)blockIdx.x * ROWS + r;
-    const bool active = row < a.rows;
-    const float2* in = reinterpret_cast<const float2*>(a.in) + row * H;
     float2 x[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) x[m] = active ? __ldg(&in[t + T * m]) : make_float2(0.f, 0.f);
-    const float2 nyq = (active && t == 0) ? __ldg(&in[L]) : make_float2(0.f, 0.f);
-    const int partner = row_partner_lane<T>(t);
-    const float2 wt = __ldg(&a.twpack[t]);
+    for (int m = 0; m < E; ++m) x[m] = active ? ld2<CG>(&in_row[t + T * m]) : make_float2(0.f, 0.f);
+    const float2 nyq = (active && t == 0) ? ld2<CG>(&in_row[L]) : make_float2(0.f, 0.f);
+    const int partner = lane - t + ((T - t) & (T - 1));
+    const float2 wt = __ldg(&twpack[t]);
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -259,16 +252,75 @@ __global__ void __launch_bounds__((L / E) * ROWS) row_c2r_warp_kernel(RowArgs a)
         }
         const float2 s = cadd(xk, xc);
         const float2 d = csub(xk, xc);
-        const float2 w = (m == 0) ? wt : cmul(wt, __ldg(&a.twpack[T * m]));
+        const float2 w = (m == 0) ? wt : cmul(wt, __ldg(&twpack[T * m]));
         const float2 wd = cmulc(d, w);  // Z = s + i W^{-k} d
         v[m] = make_float2(s.x - wd.y, s.y + wd.x);
     }
-    RowExchange<true> ex{sm + r * RS};
-    fft_group<L, E, +1>(v, t, a.tw, ex);
-    float2* out = reinterpret_cast<float2*>(a.out) + row * L;
+    RowExchange<true> ex{sm_row};
+    fft_group<L, E, +1>(v, t, tw, ex);
     if (active) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) out[t + T * m] = v[m];
+        for (int m = 0; m < E; ++m) out_row[t + T * m] = v[m];
+    }
+}
+
+template <int L, int E, int ROWS>
+__global__ void __launch_bounds__((L / E) * ROWS) row_r2c_warp_kernel(RowArgs a)
+{
+    extern __shared__ float2 sm[];
+    constexpr int T = L / E;
+    constexpr int H = L + 1;
+    const int t = threadIdx.x, r = threadIdx.y;
+    const long long row = (long long)blockIdx.x * ROWS + r;
+    row_r2c_body<L, E, false>(reinterpret_cast<const float2*>(a.in) + row * L,
+                              reinterpret_cast<float2*>(a.out) + row * H, row < a.rows, t, (r * T + t) & 31,
+                              sm + r * RowLayout<L>::stride, a.tw, a.twpack);
+}
+
+template <int L, int E, int ROWS>
+__global__ void __launch_bounds__((L / E) * ROWS) row_c2r_warp_kernel(RowArgs a)
+{
+    extern __shared__ float2 sm[];
+    constexpr int T = L / E;
+    constexpr int H = L + 1;
+    const int t = threadIdx.x, r = threadIdx.y;
+    const long long row = (long long)blockIdx.x * ROWS + r;
+    row_c2r_body<L, E, false>(reinterpret_cast<const float2*>(a.in) + row * H,
+                              reinterpret_cast<float2*>(a.out) + row * L, row < a.rows, t, (r * T + t) & 31,
+                              sm + r * RowLayout<L>::stride, a.tw, a.twpack);
+}
+
+// Column transform of one tile column: base points at element (j = 0) of the
+// column, positions t + T*m at stride S; exchange through ex.
+// Out-of-place variant: reads the column at src, writes the result at dst
+// (same layout and stride).
+template <int L, int E, int DIR, bool CG>
+__device__ __forceinline__ void col_body_to(const float2* src, float2* dst, long long S, bool active, int t,
+                                            const float2* __restrict__ tw, const ColExchange& ex)
+{
+    constexpr int T = L / E;
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = active ? ld2<CG>(&src[(long long)(t + T * m) * S]) : make_float2(0.f, 0.f);
+    fft_group<L, E, DIR>(v, t, tw, ex);
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) dst[(long long)(t + T * m) * S] = v[m];
+    }
+}
+
+template <int L, int E, int DIR, bool CG>
+__device__ __forceinline__ void col_body(float2* base, long long S, bool active, int t, const float2* __restrict__ tw,
+                                         float scale, const ColExchange& ex)
+{
+    constexpr int T = L / E;
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = active ? ld2<CG>(&base[(long long)(t + T * m) * S]) : make_float2(0.f, 0.f);
+    fft_group<L, E, DIR>(v, t, tw, ex);
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) base[(long long)(t + T * m) * S] = cscale(v[m], scale);
     }
 }
 

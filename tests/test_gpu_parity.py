@@ -149,6 +149,56 @@ def test_generic_kernels_forced(cuda_lib, shape):
     assert rel_l2(gpu_c2r(cuda_lib, Y, n2, flags=f), oracle.c2r3d(Y.astype(np.complex128), n2)) <= TOL
 
 
+@pytest.mark.parametrize("shape", [(32, 32, 32), (128, 128, 128), (64, 256, 256), (4, 512, 512)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_fused_plane_vs_three_pass(cuda_lib, shape):
+    """Shapes with a fused plane kernel, run fused and with the separate
+    row / n1 / n0 passes forced: both match the oracle."""
+    n0, n1, n2 = shape
+    x32 = synth.uniform_field(shape, seed=57).astype(np.float32)
+    Xo = oracle.r2c3d(x32.astype(np.float64))
+    Y = random_half_spectrum((n0, n1, n2 // 2 + 1), seed=59)
+    yo = oracle.c2r3d(Y.astype(np.complex128), n2)
+    for flags in (cuda_lib.FFT3D_FLAG_FUSED_PLANE, 0):
+        assert rel_l2(gpu_r2c(cuda_lib, x32, flags=flags), Xo) <= TOL
+        assert rel_l2(gpu_c2r(cuda_lib, Y, n2, flags=flags), yo) <= TOL
+    assert "plane[fused" in cuda_lib.Plan(n0, n1, n2, flags=cuda_lib.FFT3D_FLAG_FUSED_PLANE).describe()
+    assert "plane[fused" not in cuda_lib.Plan(n0, n1, n2).describe()
+
+
+def test_fused_plane_batched(cuda_lib):
+    shape = (2, 16, 32, 32)
+    x32 = synth.uniform_field(shape, seed=61).astype(np.float32)
+    f = cuda_lib.FFT3D_FLAG_FUSED_PLANE
+    X = gpu_r2c(cuda_lib, x32, flags=f)
+    for b in range(2):
+        assert rel_l2(X[b], oracle.r2c3d(x32[b].astype(np.float64))) <= TOL
+    Y = random_half_spectrum((32, 32, 17), seed=62).reshape(2, 16, 32, 17)
+    y = gpu_c2r(cuda_lib, Y, 32, flags=f)
+    for b in range(2):
+        assert rel_l2(y[b], oracle.c2r3d(Y[b].astype(np.complex128), 32)) <= TOL
+
+
+def test_bounded_wait_gives_up_without_hanging(cuda_lib):
+    """Failure detection without a GPU fault: with the test hook, the
+    producers of plane 0 never report, so the consumers' bounded waits give up
+    (about a millisecond), the kernel returns, and the host reads
+    FFT3D_ERR_TIMEOUT from the status word; the context stays usable."""
+    lib = cuda_lib
+    n = 32
+    plan = lib.Plan(n, n, n, flags=lib.FFT3D_FLAG_FUSED_PLANE | lib.FFT3D_FLAG_TEST_SKIP_ARRIVAL)
+    assert "plane[fused" in plan.describe()
+    x = torch.zeros((n, n, n), dtype=torch.float32, device="cuda")
+    X = torch.empty((n, n, n // 2 + 1), dtype=torch.complex64, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.fft3d_r2c(plan.handle, x.data_ptr(), X.data_ptr(), s) == lib.FFT3D_OK
+    assert lib.fft3d_query_device_status(plan.handle, s) == lib.FFT3D_ERR_TIMEOUT
+    # the status word was cleared by the query, and the device still works
+    assert lib.fft3d_query_device_status(plan.handle, s) == lib.FFT3D_OK
+    x32 = synth.uniform_field((n, n, n), seed=63).astype(np.float32)
+    assert rel_l2(gpu_r2c(lib, x32), oracle.r2c3d(x32.astype(np.float64))) <= TOL
+
+
 def test_batched_tma_column_pass(cuda_lib):
     shape = (3, 256, 8, 12)
     x32 = synth.uniform_field(shape, seed=39).astype(np.float32)
@@ -219,6 +269,44 @@ def test_argument_errors_leave_output_untouched(cuda_lib):
     assert lib.fft3d_r2c(xp, x.data_ptr(), out.data_ptr()) == lib.FFT3D_ERR_NO_WORKSPACE
     assert lib.fft3d_set_workspace(xp, out.data_ptr() + 16) == lib.FFT3D_ERR_MISALIGNED
     lib.fft3d_destroy(xp)
+
+
+# ---------------------------------------------------------------------------
+# FP64 device diagnostics: Parseval sum and shell energies vs the oracle.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape,batch", [((32, 32, 32), 1), ((24, 40, 36), 2), ((15, 12, 10), 1), ((64, 48, 40), 1)],
+                         ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else str(v))
+def test_energy_matches_oracle(cuda_lib, shape, batch):
+    n0, n1, n2 = shape
+    H = n2 // 2 + 1
+    Y = random_half_spectrum((batch * n0, n1, H), seed=71).reshape(batch, n0, n1, H)
+    plan = cuda_lib.Plan(n0, n1, n2, batch=batch)
+    nbins = 40
+    total, shells = plan.energy(torch.from_numpy(Y).cuda(), nbins)
+    torch.cuda.synchronize()
+    total = total.cpu().numpy()
+    shells = shells.cpu().numpy()
+    for b in range(batch):
+        Yb = Y[b].astype(np.complex128)
+        # |X|^2 is formed in FP32 on the device: relative error ~1e-7 per term
+        assert abs(total[b] - oracle.half_energy(Yb, n2)) <= 1e-6 * oracle.half_energy(Yb, n2)
+        ref = oracle.shell_energy(Yb, n0, n1, n2, nbins)
+        assert np.all(np.abs(shells[b] - ref) <= 1e-6 * np.maximum(ref, 1e-30) + 1e-12)
+        # every bin of shell < nbins is counted once
+        assert abs(shells[b].sum() - ref.sum()) <= 1e-6 * ref.sum()
+
+
+def test_energy_parseval_of_r2c(cuda_lib):
+    n = 64
+    x32 = synth.uniform_field((n, n, n), seed=73).astype(np.float32)
+    plan = cuda_lib.Plan(n, n, n)
+    xd = torch.from_numpy(x32).cuda()
+    X = torch.empty((n, n, n // 2 + 1), dtype=torch.complex64, device="cuda")
+    plan.r2c(xd.data_ptr(), X.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    total, _ = plan.energy(X, 8)
+    e = total.cpu().item() / n ** 3
+    assert abs(e - np.sum(x32.astype(np.float64) ** 2)) <= 1e-5 * e
 
 
 # ---------------------------------------------------------------------------

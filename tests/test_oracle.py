@@ -225,3 +225,27 @@ def test_spectrum_as_oracle():
     N = n0 * n1 * n2
     assert 0.3 < np.sqrt(np.mean(x * x)) < 3.0
     assert rel_l2(oracle.r2c3d(x), N * S) < 1e-13
+
+
+def test_shell_index_exact():
+    """Shell b = floor(|k| + 1/2) equals (isqrt(4|k|^2) + 1) // 2 exactly
+    (integer square root, no floating point); checked bin by bin."""
+    import math
+    n0, n1, n2 = 30, 24, 40
+    b = oracle.shell_index(n0, n1, n2)
+    for j0 in range(n0):
+        for j1 in range(n1):
+            for j2 in range(n2 // 2 + 1):
+                kk = min(j0, n0 - j0) ** 2 + min(j1, n1 - j1) ** 2 + j2 ** 2
+                assert b[j0, j1, j2] == (math.isqrt(4 * kk) + 1) // 2
+    assert b[0, 0, 0] == 0 and b[1, 0, 0] == 1 and b[0, 0, 1] == 1
+
+
+def test_shell_energy_sums_to_parseval_total():
+    n0, n1, n2 = 16, 12, 10
+    X = oracle.r2c3d(synth.uniform_field((n0, n1, n2), seed=5))
+    nb = int(np.sqrt((n0 // 2) ** 2 + (n1 // 2) ** 2 + (n2 // 2) ** 2)) + 2
+    E = oracle.shell_energy(X, n0, n1, n2, nb)
+    assert np.all(E >= 0)
+    assert abs(E.sum() - oracle.half_energy(X, n2)) < 1e-12 * E.sum()
+    assert abs(E[0] - abs(X[0, 0, 0]) ** 2) < 1e-12 * E.sum()
