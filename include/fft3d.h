@@ -190,6 +190,35 @@ double fft3d_pass_bytes(fft3d_handle plan, int pass);
  */
 int fft3d_energy(fft3d_handle plan, const void* spec, double* total, double* shells, int nbins, void* stream);
 
+/*
+ * fft3d_energy for callers that cannot allocate device memory: applications
+ * whose device memory is owned entirely by their own allocator or by a budget
+ * fixed at start-up, or code called back from inside another library's memory
+ * management, where a cudaMalloc inside a library call would fail, block, or
+ * break that budget.  The paper has no counterpart; this is an interface
+ * convenience of the library.
+ *
+ * Same inputs, outputs and definitions as fft3d_energy (spec is
+ * batch*n0*n1*(n2/2+1) float2 on the device; total and shells device
+ * doubles, either may be NULL, not both), but it takes the shape instead of a
+ * plan and allocates nothing: its scratch is one fixed array of 2^18 doubles
+ * (2 MiB) inside the library, which every GPU that loads the library holds
+ * until the process exits.  A call needs batch * B * (nbins + 1) doubles of
+ * it, B = min(256, ceil(n0*n1/8)); a larger call is rejected with
+ * FFT3D_ERR_UNSUPPORTED_SIZE before anything is launched.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  Every call on a device shares the one array, and it keeps the
+ * last call's contents (each call writes all the scratch it reads, so nothing
+ * needs clearing): calls that overlap on the GPU, e.g. on two streams without
+ * ordering between them, race and give wrong results; order them, for
+ * instance by issuing them on one stream.  Asynchronous on stream.  Reports
+ * through its return value only (fft3d_last_error is not updated).
+ */
+int fft3d_energy_noalloc(const void* spec, int n0, int n1, int n2, int batch, double* total, double* shells,
+                         int nbins, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,6 +63,7 @@ _SIGS = {
     "fft3d_pass_name": ([_I], ctypes.c_char_p),
     "fft3d_pass_bytes": ([_P, _I], ctypes.c_double),
     "fft3d_energy": ([_P, _P, _P, _P, _I, _P], _I),
+    "fft3d_energy_noalloc": ([_P, _I, _I, _I, _I, _P, _P, _I, _P], _I),
 }
 
 
@@ -195,6 +196,13 @@ def fft3d_pass_bytes(plan, pass_id):
 
 def fft3d_energy(plan, spec_ptr, total_ptr, shells_ptr, nbins, stream=0):
     return load().fft3d_energy(_v(plan), _v(spec_ptr), _v(total_ptr), _v(shells_ptr), nbins, _v(stream))
+
+
+def fft3d_energy_noalloc(spec_ptr, n0, n1, n2, batch, total_ptr, shells_ptr, nbins, stream=0):
+    """fft3d_energy without a plan and without any device allocation (fixed
+    library-owned scratch; see include/fft3d.h)."""
+    return load().fft3d_energy_noalloc(_v(spec_ptr), n0, n1, n2, batch, _v(total_ptr), _v(shells_ptr), nbins,
+                                       _v(stream))
 
 
 def error_string(status: int) -> str:
