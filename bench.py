@@ -317,6 +317,29 @@ def main():
             vp.close()
         line["variants"] = variants
 
+    # pseudo-spectral nonlinear term at 256^3 (3 velocity spectra in, 6 dealiased
+    # product spectra out), replayed as one CUDA graph
+    if not args.no_variants:
+        m = 256
+        nl = fft3d.NonlinearTerm(m, m, m)
+        import synth
+        U = torch.from_numpy(synth.spectral_velocity(m, m, m, seed=synth.seed_for_config(4)).astype(np.complex64)).to(dev)
+        out = torch.empty((6, m, m, m // 2 + 1), dtype=torch.complex64, device=dev)
+        Mc = m * m * (m // 2 + 1)
+        ns = torch.cuda.Stream(dev)
+        ns.wait_stream(stream)
+        with torch.cuda.stream(ns):
+            for _ in range(3):
+                nl(U, out=out, stream=ns)
+            reps = 50
+            nms = time_steps(lambda: nl(U, out=out, stream=ns), ns, reps) / reps
+        run_bytes = 360 * Mc        # bytes of the five passes as run (3+3 inverse, 6+6 forward, fused rows)
+        line["nonlinear_256"] = {"ms_per_application": nms, "gbs_passes_run": run_bytes / (nms * 1e-3) / 1e9,
+                                 "passes_run_bytes": run_bytes, "launches": fft3d.fft3d_nonlinear_launches(nl.handle),
+                                 "graph": True}
+        nl.close()
+        del U, out
+
     # end to end through the C ABI with host buffers: H2D of x, r2c, c2r, D2H of y
     if not args.no_e2e:
         xh = x.cpu().pin_memory()

@@ -172,6 +172,44 @@ const char* fft3d_pass_name(int pass);
 double fft3d_pass_bytes(fft3d_handle plan, int pass);
 
 /*
+ * Pseudo-spectral nonlinear term (the quadratic term of the Tarang-type
+ * solvers of Sec. 1; the paper states that FFTs take about 75% of such a
+ * solver's time).  For a velocity field given by its three half spectra
+ * uhat_i (i = 0, 1, 2) it computes the six dealiased product spectra
+ *     N_ij = mask * r2c(u_i * u_j) / N,   u_i = c2r(uhat_i),
+ *     ij in (00, 01, 02, 11, 12, 22) (in that order),
+ * mask = the 2/3 rule: keep bin k iff 3|k_a| < n_a on every axis, with k_a the
+ * signed wavenumber in [-n_a/2, n_a/2) (Nyquist bins always dropped).
+ * Five launches, batched over the fields: n0 inverse x3 (out of place into the
+ * workspace), n1 inverse x3, one row kernel doing the three c2r, the six
+ * products in registers and the six r2c (k2 part of the mask), n1 forward x6
+ * (k1 part), n0 forward x6 (k0 part and 1/N).  On a non-default stream the
+ * sequence is captured once into a CUDA graph per (uhat, nhat, workspace) and
+ * replayed; on the legacy default stream it is launched directly.
+ * Supported when n2/2 has a warp-resident row kernel (n2/2 in 8..512 of the
+ * built lengths); else fft3d_nonlinear_plan fails with UNSUPPORTED_SIZE.
+ */
+typedef struct fft3d_nl_s* fft3d_nl_handle;
+
+/* Plan for n0 x n1 x n2 fields (blocks; NULL on error, see fft3d_last_error). */
+fft3d_nl_handle fft3d_nonlinear_plan(int n0, int n1, int n2);
+
+/* Caller workspace: 3 * n0 * n1 * (n2/2+1) complex64 values. */
+size_t fft3d_nonlinear_workspace_bytes(fft3d_nl_handle nl);
+int fft3d_nonlinear_set_workspace(fft3d_nl_handle nl, void* dev_ptr);
+
+/* uhat: 3 contiguous half spectra (device, read only, preserved);
+ * nhat: 6 contiguous half spectra (device, written); 16-byte aligned; none
+ * of uhat, nhat and the workspace may overlap. */
+int fft3d_nonlinear_exec(fft3d_nl_handle nl, const void* uhat, void* nhat, void* stream);
+
+/* Kernel launches per fft3d_nonlinear_exec. */
+int fft3d_nonlinear_launches(fft3d_nl_handle nl);
+
+/* NULL-safe; blocks on the device. */
+void fft3d_nonlinear_destroy(fft3d_nl_handle nl);
+
+/*
  * FP64 spectral diagnostics of a half spectrum (device-side checks of a
  * transform, and the energy spectrum of a pseudo-spectral solver, Sec. 1).
  * spec:   batch*n0*n1*H float2 (device), read only, laid out as fft3d_r2c

@@ -64,6 +64,12 @@ _SIGS = {
     "fft3d_pass_bytes": ([_P, _I], ctypes.c_double),
     "fft3d_energy": ([_P, _P, _P, _P, _I, _P], _I),
     "fft3d_energy_noalloc": ([_P, _I, _I, _I, _I, _P, _P, _I, _P], _I),
+    "fft3d_nonlinear_plan": ([_I, _I, _I], _P),
+    "fft3d_nonlinear_workspace_bytes": ([_P], ctypes.c_size_t),
+    "fft3d_nonlinear_set_workspace": ([_P, _P], _I),
+    "fft3d_nonlinear_exec": ([_P, _P, _P, _P], _I),
+    "fft3d_nonlinear_launches": ([_P], _I),
+    "fft3d_nonlinear_destroy": ([_P], None),
 }
 
 
@@ -203,6 +209,69 @@ def fft3d_energy_noalloc(spec_ptr, n0, n1, n2, batch, total_ptr, shells_ptr, nbi
     library-owned scratch; see include/fft3d.h)."""
     return load().fft3d_energy_noalloc(_v(spec_ptr), n0, n1, n2, batch, _v(total_ptr), _v(shells_ptr), nbins,
                                        _v(stream))
+
+
+def fft3d_nonlinear_plan(n0, n1, n2):
+    return load().fft3d_nonlinear_plan(n0, n1, n2)
+
+
+def fft3d_nonlinear_workspace_bytes(nl):
+    return load().fft3d_nonlinear_workspace_bytes(_v(nl))
+
+
+def fft3d_nonlinear_set_workspace(nl, dev_ptr):
+    return load().fft3d_nonlinear_set_workspace(_v(nl), _v(dev_ptr))
+
+
+def fft3d_nonlinear_exec(nl, uhat_ptr, nhat_ptr, stream=0):
+    return load().fft3d_nonlinear_exec(_v(nl), _v(uhat_ptr), _v(nhat_ptr), _v(stream))
+
+
+def fft3d_nonlinear_launches(nl):
+    return load().fft3d_nonlinear_launches(_v(nl))
+
+
+def fft3d_nonlinear_destroy(nl):
+    load().fft3d_nonlinear_destroy(_v(nl))
+
+
+class NonlinearTerm:
+    """Owning wrapper of fft3d_nonlinear_*: workspace from torch, then
+    __call__(uhat (3, n0, n1, H) complex64 CUDA) -> (6, n0, n1, H) complex64."""
+
+    def __init__(self, n0, n1, n2):
+        import torch
+        h = fft3d_nonlinear_plan(n0, n1, n2)
+        if not h:
+            raise Fft3dError(fft3d_last_error(), "fft3d_nonlinear_plan")
+        self.handle = h
+        self.shape = (n0, n1, n2)
+        self._ws = torch.empty(fft3d_nonlinear_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+        st = fft3d_nonlinear_set_workspace(h, self._ws.data_ptr())
+        if st != FFT3D_OK:
+            raise Fft3dError(st, "fft3d_nonlinear_set_workspace")
+
+    def __call__(self, uhat, out=None, stream=None):
+        import torch
+        n0, n1, n2 = self.shape
+        if out is None:
+            out = torch.empty((6, n0, n1, n2 // 2 + 1), dtype=torch.complex64, device=uhat.device)
+        st = fft3d_nonlinear_exec(self.handle, uhat.data_ptr(), out.data_ptr(),
+                                  _stream_ptr(stream) if stream is not False else 0)
+        if st != FFT3D_OK:
+            raise Fft3dError(st, "fft3d_nonlinear_exec")
+        return out
+
+    def close(self):
+        if self.handle:
+            fft3d_nonlinear_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def error_string(status: int) -> str:

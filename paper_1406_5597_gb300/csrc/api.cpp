@@ -162,9 +162,9 @@ struct fft3d_plan_s {
     // tensor maps of recent column-pass operands, keyed by (base, stride)
     struct MapCache {
         const void* base = nullptr;
-        long long S = 0;
+        long long S = 0, C = 0, nb = 0;
         CUtensorMap map;
-    } maps[4];
+    } maps[8];
     int next_map = 0;
 };
 
@@ -237,16 +237,32 @@ bool tma_ok(const fft3d_plan_s* p, const Axis& a, long long S, long long C, long
 const CUtensorMap* tensor_map(fft3d_plan_s* p, const Axis& a, const ColArgs& ca)
 {
     for (auto& m : p->maps)
-        if (m.base == ca.data && m.S == ca.S) return &m.map;
+        if (m.base == ca.data && m.S == ca.S && m.C == ca.C && m.nb == ca.nb) return &m.map;
     auto& m = p->maps[p->next_map];
-    p->next_map = (p->next_map + 1) % 4;
+    p->next_map = (p->next_map + 1) % 8;
     if (col_tensor_map_host(&m.map, ca, a.L, a.spec->tma_W) != cudaSuccess) {
         m.base = nullptr;
         return nullptr;
     }
     m.base = ca.data;
     m.S = ca.S;
+    m.C = ca.C;
+    m.nb = ca.nb;
     return &m.map;
+}
+
+// One column pass with full control of the arguments (destination, mask, scale).
+cudaError_t launch_col_args(fft3d_plan_s* p, const Axis& a, int dir, const ColArgs& ca, cudaStream_t s)
+{
+    if (a.L <= 1) {  // length-1 axis: the transform is the identity (apart from scale / mask / destination)
+        if (!ca.dst && ca.scale == 1.0f) return cudaSuccess;
+    }
+    if (uses_generic(p, a, false)) return generic_col(ca, a.gen, dir, s);
+    if (tma_ok(p, a, ca.S, ca.C, ca.Bs)) {
+        if (const CUtensorMap* m = tensor_map(p, a, ca))
+            return dir < 0 ? a.spec->tma_fwd(ca, *m, s) : a.spec->tma_inv(ca, *m, s);
+    }
+    return dir < 0 ? a.spec->col_fwd(ca, s) : a.spec->col_inv(ca, s);
 }
 
 cudaError_t run_col(fft3d_plan_s* p, const Axis& a, int dir, float2* data, long long S, long long C,
@@ -255,13 +271,8 @@ cudaError_t run_col(fft3d_plan_s* p, const Axis& a, int dir, float2* data, long 
     if (a.L <= 1) return cudaSuccess;
     const bool n0axis = (&a == &p->ax0);
     ProfScope ps(p, n0axis ? (dir < 0 ? PASS_N0_FWD : PASS_N0_INV) : (dir < 0 ? PASS_N1_FWD : PASS_N1_INV), s);
-    ColArgs ca{data, S, C, nb, Bs, a.d_tw, 1.0f, p->d_status};
-    if (uses_generic(p, a, false)) return generic_col(ca, a.gen, dir, s);
-    if (tma_ok(p, a, S, C, Bs)) {
-        if (const CUtensorMap* m = tensor_map(p, a, ca))
-            return dir < 0 ? a.spec->tma_fwd(ca, *m, s) : a.spec->tma_inv(ca, *m, s);
-    }
-    return dir < 0 ? a.spec->col_fwd(ca, s) : a.spec->col_inv(ca, s);
+    ColArgs ca{data, S, C, nb, Bs, a.d_tw, 1.0f, p->d_status, nullptr, 0};
+    return launch_col_args(p, a, dir, ca, s);
 }
 
 cudaError_t run_row(fft3d_plan_s* p, int dir, const void* in, void* out, cudaStream_t s)
@@ -619,6 +630,152 @@ int fft3d_energy(fft3d_handle p, const void* spec, double* total, double* shells
                       (cudaStream_t)stream) != cudaSuccess)
         return fail(FFT3D_ERR_CUDA);
     return FFT3D_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pseudo-spectral nonlinear term.
+// ---------------------------------------------------------------------------
+struct fft3d_nl_s {
+    fft3d_plan_s* plan = nullptr;  // batch-1 plan: twiddles and kernel choices
+    void* workspace = nullptr;     // 3 * M complex, lent by the caller
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void* g_uhat = nullptr;  // operands the graph was captured with
+    void* g_nhat = nullptr;
+    void* g_ws = nullptr;
+};
+
+namespace {
+
+cudaError_t enqueue_nonlinear(fft3d_nl_s* nl, const void* uhat, void* nhat, cudaStream_t s)
+{
+    fft3d_plan_s* p = nl->plan;
+    const long long H = p->H, n0 = p->n0, n1 = p->n1, M = p->M, P = p->P;
+    float2* W = (float2*)nl->workspace;
+    float2* U = (float2*)const_cast<void*>(uhat);
+    float2* Nh = (float2*)nhat;
+    cudaError_t e;
+    // 1. n0 inverse of the three fields, out of place into the workspace (uhat is preserved)
+    if (p->n0 > 1) {
+        ColArgs c{U, P, P, 3, M, p->ax0.d_tw, 1.0f, p->d_status, W, 0};
+        if ((e = launch_col_args(p, p->ax0, +1, c, s)) != cudaSuccess) return e;
+    } else if ((e = cudaMemcpyAsync(W, U, 3 * M * sizeof(float2), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+        return e;
+    }
+    // 2. n1 inverse of the three fields, in place
+    if (p->n1 > 1) {
+        ColArgs c{W, H, H, 3 * n0, n1 * H, p->ax1.d_tw, 1.0f, p->d_status, nullptr, 0};
+        if ((e = launch_col_args(p, p->ax1, +1, c, s)) != cudaSuccess) return e;
+    }
+    // 3. rows: three c2r, six products, six r2c with the 2/3 rule on k2
+    NlRowArgs r{W, Nh, n0 * n1, M, p->ax2.d_tw, p->d_twpack, (p->n2 + 2) / 3};
+    if ((e = p->ax2.spec->nl(r, s)) != cudaSuccess) return e;
+    // 4. n1 forward of the six products, 2/3 rule on k1
+    {
+        ColArgs c{Nh, H, H, 6 * n0, n1 * H, p->ax1.d_tw, 1.0f, p->d_status, nullptr, 1};
+        if ((e = launch_col_args(p, p->ax1, -1, c, s)) != cudaSuccess) return e;
+    }
+    // 5. n0 forward, 2/3 rule on k0 and the 1/N normalisation
+    {
+        ColArgs c{Nh, P, P, 6, M, p->ax0.d_tw, 1.0f / (float)p->N, p->d_status, nullptr, 1};
+        if ((e = launch_col_args(p, p->ax0, -1, c, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void drop_graph(fft3d_nl_s* nl)
+{
+    if (nl->exec) cudaGraphExecDestroy(nl->exec);
+    if (nl->graph) cudaGraphDestroy(nl->graph);
+    nl->exec = nullptr;
+    nl->graph = nullptr;
+    nl->g_uhat = nullptr;
+    nl->g_nhat = nullptr;
+    nl->g_ws = nullptr;
+}
+
+}  // namespace
+
+fft3d_nl_handle fft3d_nonlinear_plan(int n0, int n1, int n2)
+{
+    fft3d_handle p = fft3d_plan_variant(n0, n1, n2, FFT3D_F32, 1, 0);
+    if (!p) return nullptr;
+    // the 1D passes are per axis; the 2/3 rule needs n1 and n0 passes that apply it
+    if (!p->ax2.spec || p->ax2.spec->nl == nullptr || (p->flags & FFT3D_FLAG_GENERIC)) {
+        fft3d_destroy(p);
+        fail(FFT3D_ERR_UNSUPPORTED_SIZE);
+        return nullptr;
+    }
+    fft3d_nl_s* nl = new (std::nothrow) fft3d_nl_s();
+    if (!nl) {
+        fft3d_destroy(p);
+        fail(FFT3D_ERR_ALLOC);
+        return nullptr;
+    }
+    nl->plan = p;
+    return nl;
+}
+
+size_t fft3d_nonlinear_workspace_bytes(fft3d_nl_handle nl)
+{
+    return nl ? (size_t)3 * (size_t)nl->plan->M * sizeof(float2) : 0;
+}
+
+int fft3d_nonlinear_set_workspace(fft3d_nl_handle nl, void* dev_ptr)
+{
+    if (!nl) return fail(FFT3D_ERR_INVALID_ARG);
+    if (dev_ptr && ((uintptr_t)dev_ptr & 255)) return fail(FFT3D_ERR_MISALIGNED);
+    nl->workspace = dev_ptr;
+    return FFT3D_OK;
+}
+
+int fft3d_nonlinear_exec(fft3d_nl_handle nl, const void* uhat, void* nhat, void* stream)
+{
+    if (!nl || !uhat || !nhat) return fail(FFT3D_ERR_INVALID_ARG);
+    if (!nl->workspace) return fail(FFT3D_ERR_NO_WORKSPACE);
+    if (((uintptr_t)uhat & 15) || ((uintptr_t)nhat & 15)) return fail(FFT3D_ERR_MISALIGNED);
+    const size_t M8 = (size_t)nl->plan->M * sizeof(float2);
+    if (overlaps(uhat, 3 * M8, nhat, 6 * M8) || overlaps(uhat, 3 * M8, nl->workspace, 3 * M8) ||
+        overlaps(nhat, 6 * M8, nl->workspace, 3 * M8))
+        return fail(FFT3D_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!s) {  // the legacy default stream cannot be captured: launch directly
+        return enqueue_nonlinear(nl, uhat, nhat, s) == cudaSuccess ? FFT3D_OK : fail(FFT3D_ERR_CUDA);
+    }
+    if (!(nl->exec && nl->g_uhat == uhat && nl->g_nhat == nhat && nl->g_ws == nl->workspace)) {
+        drop_graph(nl);
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        const cudaError_t e = enqueue_nonlinear(nl, uhat, nhat, s);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            return fail(FFT3D_ERR_CUDA);
+        }
+        nl->graph = g;
+        if (cudaGraphInstantiate(&nl->exec, g, 0) != cudaSuccess) {
+            drop_graph(nl);
+            return fail(FFT3D_ERR_CUDA);
+        }
+        nl->g_uhat = uhat;
+        nl->g_nhat = nhat;
+        nl->g_ws = nl->workspace;
+    }
+    return cudaGraphLaunch(nl->exec, s) == cudaSuccess ? FFT3D_OK : fail(FFT3D_ERR_CUDA);
+}
+
+int fft3d_nonlinear_launches(fft3d_nl_handle nl)
+{
+    return nl ? 5 : fail(FFT3D_ERR_INVALID_ARG);
+}
+
+void fft3d_nonlinear_destroy(fft3d_nl_handle nl)
+{
+    if (!nl) return;
+    cudaDeviceSynchronize();
+    drop_graph(nl);
+    fft3d_destroy(nl->plan);
+    delete nl;
 }
 
 int fft3d_set_profiling(fft3d_handle p, int enable)

@@ -15,7 +15,20 @@ struct ColArgs {
     const float2* tw;    // W_L^m, m in [0, L)
     float scale;         // multiplies the result (1 for a plain pass)
     int* status;         // device status word (bounded waits that give up set bits here)
+    float2* dst;         // result goes here (same layout) instead of in place; nullptr: in place
+    int mask23;          // nonzero: zero the outputs whose signed index k has 3|k| >= L (2/3 rule)
 };
+
+// Output factor of a column pass for output index k of a length-L axis:
+// scale, or 0 where the 2/3 rule drops k (signed k in [-L/2, L/2), so the
+// Nyquist bin is always dropped).
+__host__ __device__ inline float col_out_factor(int k, int L, float scale, int mask23)
+{
+    if (!mask23) return scale;
+    const int ks = (2 * k < L) ? k : k - L;
+    const int ak = ks < 0 ? -ks : ks;
+    return (3 * ak < L) ? scale : 0.f;
+}
 
 // Device status bits.
 constexpr int kStatusTimeout = 1;
@@ -38,6 +51,17 @@ struct GenPlan {
 using ColFn = cudaError_t (*)(const ColArgs&, cudaStream_t);
 using ColTmaFn = cudaError_t (*)(const ColArgs&, const CUtensorMap&, cudaStream_t);
 using RowFn = cudaError_t (*)(const RowArgs&, cudaStream_t);
+struct NlRowArgs {
+    const float2* in;
+    float2* out;
+    long long rows;
+    long long fs;  // field stride (complex elements)
+    const float2* tw;
+    const float2* twpack;
+    int k2_keep;   // bins k2 >= k2_keep are set to zero
+};
+
+using NlFn = cudaError_t (*)(const NlRowArgs&, cudaStream_t);
 
 // Compile-time specialised kernels for one transform length.
 struct LenEntry {
@@ -49,6 +73,7 @@ struct LenEntry {
     int row_E, row_rows;  // row kernels (row_E = 0: none)
     bool row_warp;        // rows resident in warps (shuffle unpack) or staged in shared memory
     RowFn r2c, c2r;
+    NlFn nl;              // fused nonlinear-term row kernel (warp rows only)
 };
 
 const LenEntry* find_len(int L);

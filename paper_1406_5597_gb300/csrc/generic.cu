@@ -71,9 +71,11 @@ __global__ void generic_col_kernel(ColArgs a, GenPlan g, int G)
     }
     __syncthreads();
     float2* res = generic_stages<DIR>(g, b0, b1, G, a.tw);
+    float2* out = (a.dst ? a.dst : a.data) + b * a.Bs + c0;
     for (int i = tid; i < L * G; i += nthr) {
         const int line = i % G, p = i / G;
-        if (c0 + line < a.C) base[(long long)p * a.S + line] = cscale(res[gi(p, line, G)], a.scale);
+        if (c0 + line < a.C)
+            out[(long long)p * a.S + line] = cscale(res[gi(p, line, G)], col_out_factor(p, L, a.scale, a.mask23));
     }
 }
 

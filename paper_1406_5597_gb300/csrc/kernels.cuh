@@ -46,8 +46,10 @@ __global__ void __launch_bounds__(MAXT) col_kernel(ColArgs a, int W)
     ColExchange ex{sm, W, c};
     fft_group<L, E, DIR>(v, t, a.tw, ex);
     if (active) {
+        float2* out = (a.dst ? a.dst : a.data) + b * a.Bs + c0 + c;
 #pragma unroll
-        for (int m = 0; m < E; ++m) base[(long long)(t + T * m) * a.S] = cscale(v[m], a.scale);
+        for (int m = 0; m < E; ++m)
+            out[(long long)(t + T * m) * a.S] = cscale(v[m], col_out_factor(t + T * m, L, a.scale, a.mask23));
     }
 }
 
@@ -185,19 +187,19 @@ __device__ __forceinline__ float2 ld2(const float2* p)
     else return __ldg(p);
 }
 
-// r2c of one row: in_row = packed row (L float2), out_row = H bins.  t in
-// [0, T), lane = this thread's lane in its warp; the T threads of a row are
-// consecutive lanes.  sm_row: RowLayout<L>::stride float2 of exchange space.
-template <int L, int E, bool CG>
-__device__ __forceinline__ void row_r2c_body(const float2* in_row, float2* out_row, bool active, int t, int lane,
+// r2c of one packed real row held in registers (v[m] = samples 2p, 2p+1 at
+// position p = t + T*m): forward FFT, Hermitian unpack, then store of the H
+// bins to out_row, with bins k2 >= k2_keep set to zero (k2_keep = L+1 keeps
+// all; the 2/3 rule keeps 3*k2 < n2).  t in [0, T); lane = the thread's lane;
+// the T threads of a row are consecutive lanes.  sm_row: RowLayout<L>::stride
+// float2 of exchange space.
+template <int L, int E>
+__device__ __forceinline__ void row_r2c_regs(float2 (&v)[E], float2* out_row, bool active, int t, int lane,
                                              float2* sm_row, const float2* __restrict__ tw,
-                                             const float2* __restrict__ twpack)
+                                             const float2* __restrict__ twpack, int k2_keep = L + 1)
 {
     constexpr int T = L / E;
     static_assert(T <= 32 && (32 % T) == 0, "rows must pack into warps");
-    float2 v[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = active ? ld2<CG>(&in_row[t + T * m]) : make_float2(0.f, 0.f);
     RowExchange<true> ex{sm_row};
     fft_group<L, E, -1>(v, t, tw, ex);
     const int partner = lane - t + ((T - t) & (T - 1));
@@ -213,16 +215,32 @@ __device__ __forceinline__ void row_r2c_body(const float2* in_row, float2* out_r
         const float2 d = csub(zk, zc);
         const float2 w = (m == 0) ? wt : cmul(wt, __ldg(&twpack[T * m]));
         const float2 wd = cmul(d, w);  // X = s/2 - (i/2) W^k d
-        if (active) out_row[t + T * m] = make_float2(0.5f * (s.x + wd.y), 0.5f * (s.y - wd.x));
+        const int k = t + T * m;
+        if (active)
+            out_row[k] = (k < k2_keep) ? make_float2(0.5f * (s.x + wd.y), 0.5f * (s.y - wd.x)) : make_float2(0.f, 0.f);
     }
-    if (active && t == 0) out_row[L] = make_float2(v[0].x - v[0].y, 0.f);
+    if (active && t == 0) out_row[L] = (L < k2_keep) ? make_float2(v[0].x - v[0].y, 0.f) : make_float2(0.f, 0.f);
 }
 
-// c2r of one row: in_row = H bins, out_row = packed real row (L float2).
+// r2c of one row: in_row = packed row (L float2), out_row = H bins.
 template <int L, int E, bool CG>
-__device__ __forceinline__ void row_c2r_body(const float2* in_row, float2* out_row, bool active, int t, int lane,
+__device__ __forceinline__ void row_r2c_body(const float2* in_row, float2* out_row, bool active, int t, int lane,
                                              float2* sm_row, const float2* __restrict__ tw,
                                              const float2* __restrict__ twpack)
+{
+    constexpr int T = L / E;
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = active ? ld2<CG>(&in_row[t + T * m]) : make_float2(0.f, 0.f);
+    row_r2c_regs<L, E>(v, out_row, active, t, lane, sm_row, tw, twpack);
+}
+
+// c2r of one row of H bins into registers: v[m] = the real samples 2p, 2p+1
+// at position p = t + T*m (unnormalised).
+template <int L, int E, bool CG>
+__device__ __forceinline__ void row_c2r_regs(const float2* in_row, bool active, int t, int lane, float2* sm_row,
+                                             const float2* __restrict__ tw, const float2* __restrict__ twpack,
+                                             float2 (&v)[E])
 {
     constexpr int T = L / E;
     static_assert(T <= 32 && (32 % T) == 0, "rows must pack into warps");
@@ -232,7 +250,6 @@ __device__ __forceinline__ void row_c2r_body(const float2* in_row, float2* out_r
     const float2 nyq = (active && t == 0) ? ld2<CG>(&in_row[L]) : make_float2(0.f, 0.f);
     const int partner = lane - t + ((T - t) & (T - 1));
     const float2 wt = __ldg(&twpack[t]);
-    float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         float2 g;
@@ -258,10 +275,70 @@ __device__ __forceinline__ void row_c2r_body(const float2* in_row, float2* out_r
     }
     RowExchange<true> ex{sm_row};
     fft_group<L, E, +1>(v, t, tw, ex);
+}
+
+// c2r of one row: in_row = H bins, out_row = packed real row (L float2).
+template <int L, int E, bool CG>
+__device__ __forceinline__ void row_c2r_body(const float2* in_row, float2* out_row, bool active, int t, int lane,
+                                             float2* sm_row, const float2* __restrict__ tw,
+                                             const float2* __restrict__ twpack)
+{
+    constexpr int T = L / E;
+    float2 v[E];
+    row_c2r_regs<L, E, CG>(in_row, active, t, lane, sm_row, tw, twpack, v);
     if (active) {
 #pragma unroll
         for (int m = 0; m < E; ++m) out_row[t + T * m] = v[m];
     }
+}
+
+// Pseudo-spectral quadratic products of one row set (the nonlinear term of a
+// velocity field, Sec. 1's solver context): the three velocity rows (after
+// their n0 and n1 inverse passes) are taken to real space (c2r), the six
+// products u_i u_j (ij = 00, 01, 02, 11, 12, 22) formed sample by sample in
+// registers, and each product row transformed back (r2c) with the 2/3 rule on
+// k2 applied.  in: 3 fields of rows x H bins (field stride fs); out: 6 fields.
+
+template <int L, int E, int ROWS>
+__global__ void __launch_bounds__((L / E) * ROWS) row_nonlinear_kernel(NlRowArgs a)
+{
+    extern __shared__ float2 sm[];
+    constexpr int T = L / E;
+    constexpr int H = L + 1;
+    const int t = threadIdx.x, r = threadIdx.y;
+    const int lane = (r * T + t) & 31;
+    const long long row = (long long)blockIdx.x * ROWS + r;
+    const bool active = row < a.rows;
+    float2* smr = sm + r * RowLayout<L>::stride;
+    float2 u[3][E];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) row_c2r_regs<L, E, false>(a.in + f * a.fs + row * H, active, t, lane, smr, a.tw,
+                                                          a.twpack, u[f]);
+    constexpr int PI[6] = {0, 0, 0, 1, 1, 2};
+    constexpr int PJ[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        float2 z[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+            z[m] = make_float2(u[PI[q]][m].x * u[PJ[q]][m].x, u[PI[q]][m].y * u[PJ[q]][m].y);
+        row_r2c_regs<L, E>(z, a.out + q * a.fs + row * H, active, t, lane, smr, a.tw, a.twpack, a.k2_keep);
+    }
+}
+
+template <int L, int E, int ROWS>
+inline size_t row_smem();
+
+template <int L, int E, int ROWS>
+inline cudaError_t launch_row_nonlinear(const NlRowArgs& a, cudaStream_t s)
+{
+    constexpr int T = L / E;
+    static_assert((T * ROWS) % 32 == 0, "the shuffles need whole warps");
+    const size_t smem = row_smem<L, E, ROWS>();
+    const long long blocks = (a.rows + ROWS - 1) / ROWS;
+    if (blocks <= 0) return cudaSuccess;
+    row_nonlinear_kernel<L, E, ROWS><<<(unsigned)blocks, dim3(T, ROWS), smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int L, int E, int ROWS>
@@ -489,9 +566,10 @@ __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constan
         fft_group<L, E, DIR>(v, t, a.tw, exch);
         fence_proxy_async_smem();  // order this thread's shared accesses before the slot's next bulk copy
         if (active) {
-            float2* dst = a.data + b * a.Bs + c0 + c;
+            float2* dst = (a.dst ? a.dst : a.data) + b * a.Bs + c0 + c;
 #pragma unroll
-            for (int m = 0; m < E; ++m) dst[(long long)(t + T * m) * a.S] = cscale(v[m], a.scale);
+            for (int m = 0; m < E; ++m)
+                dst[(long long)(t + T * m) * a.S] = cscale(v[m], col_out_factor(t + T * m, L, a.scale, a.mask23));
         }
         if (++stage == STAGES) {
             stage = 0;

@@ -50,6 +50,14 @@ def test_plan_rejects_bad_dtype_batch_flags(lib):
     assert not fft3d.fft3d_plan_variant(8, 8, 8, 0, 1, 0x100)
 
 
+def test_nonlinear_plan_rejects_bad_sizes(lib):
+    assert not fft3d.fft3d_nonlinear_plan(8, 8, 7)
+    assert fft3d.fft3d_last_error() == fft3d.FFT3D_ERR_UNSUPPORTED_SIZE
+    assert fft3d.fft3d_nonlinear_exec(None, 16, 32) == fft3d.FFT3D_ERR_INVALID_ARG
+    assert fft3d.fft3d_nonlinear_workspace_bytes(None) == 0
+    fft3d.fft3d_nonlinear_destroy(None)
+
+
 def test_null_handles(lib):
     assert fft3d.fft3d_r2c(None, 16, 32) == fft3d.FFT3D_ERR_INVALID_ARG
     assert fft3d.fft3d_c2r(None, 16, 32) == fft3d.FFT3D_ERR_INVALID_ARG

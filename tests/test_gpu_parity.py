@@ -272,6 +272,64 @@ def test_argument_errors_leave_output_untouched(cuda_lib):
 
 
 # ---------------------------------------------------------------------------
+# Pseudo-spectral nonlinear term: tolerance 1e-5 rel-L2 per output field
+# (three inverse and one forward FP32 transform compose).
+# ---------------------------------------------------------------------------
+TOL_NL = 1e-5
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (32, 48, 64), (256, 256, 256)], ids=lambda s: "x".join(map(str, s)))
+def test_nonlinear_term_matches_oracle(cuda_lib, shape):
+    n0, n1, n2 = shape
+    U = synth.spectral_velocity(n0, n1, n2, seed=synth.seed_for_config(4))
+    U64 = U.astype(np.complex64)
+    ref = oracle.nonlinear_term(U64.astype(np.complex128), n2)
+    nl = cuda_lib.NonlinearTerm(n0, n1, n2)
+    ud = torch.from_numpy(U64).cuda()
+    u_before = ud.clone()
+    out = torch.empty((6, n0, n1, n2 // 2 + 1), dtype=torch.complex64, device="cuda")
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    results = []
+    with torch.cuda.stream(stream):
+        nl(ud, out=out, stream=stream)   # first call: captured into a graph and launched
+        results.append(out.clone())
+        out.zero_()
+        nl(ud, out=out, stream=stream)   # same operands: the graph is replayed
+        results.append(out.clone())
+    stream.synchronize()
+    results.append(nl(ud, stream=False))  # legacy default stream: direct launches
+    torch.cuda.synchronize()
+    assert torch.equal(ud, u_before)     # the input spectra are preserved
+    for r in results:
+        got = r.cpu().numpy().astype(np.complex128)
+        for q in range(6):
+            assert rel_l2(got[q], ref[q]) <= TOL_NL, q
+    mask = oracle.dealias_mask(n0, n1, n2)
+    assert np.all(results[0].cpu().numpy()[:, ~mask] == 0)
+    nl.close()
+
+
+def test_nonlinear_term_recaptures_for_new_buffers(cuda_lib):
+    n = 32
+    U = synth.spectral_velocity(n, n, n, seed=77).astype(np.complex64)
+    V = synth.spectral_velocity(n, n, n, seed=78).astype(np.complex64)
+    nl = cuda_lib.NonlinearTerm(n, n, n)
+    Ud, Vd = torch.from_numpy(U).cuda(), torch.from_numpy(V).cuda()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        a = nl(Ud, stream=s)
+        b = nl(Vd, stream=s)
+    s.synchronize()
+    for x, ref in ((a, oracle.nonlinear_term(U.astype(np.complex128), n)),
+                   (b, oracle.nonlinear_term(V.astype(np.complex128), n))):
+        got = x.cpu().numpy().astype(np.complex128)
+        assert max(rel_l2(got[q], ref[q]) for q in range(6)) <= TOL_NL
+    nl.close()
+
+
+# ---------------------------------------------------------------------------
 # FP64 device diagnostics: Parseval sum and shell energies vs the oracle.
 # ---------------------------------------------------------------------------
 

@@ -249,3 +249,34 @@ def test_shell_energy_sums_to_parseval_total():
     assert np.all(E >= 0)
     assert abs(E.sum() - oracle.half_energy(X, n2)) < 1e-12 * E.sum()
     assert abs(E[0] - abs(X[0, 0, 0]) ** 2) < 1e-12 * E.sum()
+
+
+def test_nonlinear_term_single_mode_closed_form():
+    """u = (cos(2 pi a j0 / n0), 0, 0): u0^2 = 1/2 + cos(2 pi 2a j0 / n0)/2, so
+    N_00 = 1/2 at k = 0 and 1/4 at k0 = +-2a (kept by the 2/3 rule iff
+    3*2a < n0), every other product zero."""
+    n0, n1, n2 = 24, 12, 10
+    N = n0 * n1 * n2
+    for a, kept in ((2, True), (5, False)):
+        u0 = synth.cosine_mode(n0, n1, n2, a, 0, 0)
+        uhat = np.zeros((3, n0, n1, n2 // 2 + 1), dtype=np.complex128)
+        uhat[0] = oracle.r2c3d(u0) / N  # so that c2r(uhat0) = u0
+        out = oracle.nonlinear_term(uhat, n2)
+        E = np.zeros_like(out[0])
+        E[0, 0, 0] = 0.5
+        if kept:
+            E[2 * a, 0, 0] = 0.25
+            E[n0 - 2 * a, 0, 0] = 0.25
+        assert np.max(np.abs(out[0] - E)) < 1e-14
+        assert np.max(np.abs(out[1:])) < 1e-14
+
+
+def test_dealias_mask_counts():
+    """The 2/3 rule keeps |k_a| <= (n_a - 1) // 3 on each axis (Nyquist dropped)."""
+    m = oracle.dealias_mask(24, 12, 10)
+    assert m.shape == (24, 12, 6)
+    keep0 = 2 * ((24 - 1) // 3) + 1
+    keep1 = 2 * ((12 - 1) // 3) + 1
+    keep2 = (10 - 1) // 3 + 1
+    assert m.sum() == keep0 * keep1 * keep2
+    assert not m[12].any() and not m[:, 6].any()
