@@ -340,6 +340,37 @@ def main():
         nl.close()
         del U, out
 
+    # grouped uneven batch: 64^3, 96^3, 128^3, 192^3, 160^3 x 4 fields, r2c + c2r,
+    # each direction one graph launch, shapes autotuned
+    if not args.no_variants:
+        gdims = [(64, 64, 64), (96, 96, 96), (128, 128, 128), (192, 192, 192), (160, 160, 160)]
+        grp = fft3d.Group(gdims, [4] * len(gdims))
+        gin, gmid, gout = [], [], []
+        for (a0, a1, a2) in gdims:
+            gin.append(torch.randn((4, a0, a1, a2), device=dev))
+            gmid.append(torch.empty((4, a0, a1, a2 // 2 + 1), dtype=torch.complex64, device=dev))
+            gout.append(torch.empty((4, a0, a1, a2), device=dev))
+        for i in range(len(gdims)):
+            fft3d.fft3d_autotune(fft3d.fft3d_group_plan_at(grp.handle, i), gin[i].data_ptr(), gmid[i].data_ptr(), 3,
+                                 sptr)
+        gs = torch.cuda.Stream(dev)
+        gs.wait_stream(stream)
+        with torch.cuda.stream(gs):
+            def gstep():
+                grp.r2c(gin, gmid, stream=gs.cuda_stream)
+                grp.c2r(gmid, gout, stream=gs.cuda_stream)
+            for _ in range(3):
+                gstep()
+            reps = 50
+            gms = time_steps(gstep, gs, reps) / reps
+        gbytes = sum(2 * 4 * (4 * a0 * a1 * a2 + 40 * a0 * a1 * (a2 // 2 + 1)) for (a0, a1, a2) in gdims)
+        line["grouped_uneven"] = {"us_per_r2c_c2r": gms * 1e3, "gbs_passes_run": gbytes / (gms * 1e-3) / 1e9,
+                                  "sizes": [f"{a}^3" for (a, _, _) in gdims], "fields_per_size": 4,
+                                  "launches": fft3d.fft3d_group_launches(grp.handle, -1)
+                                  + fft3d.fft3d_group_launches(grp.handle, 1), "graphs_per_step": 2}
+        grp.close()
+        del gin, gmid, gout
+
     # end to end through the C ABI with host buffers: H2D of x, r2c, c2r, D2H of y
     if not args.no_e2e:
         xh = x.cpu().pin_memory()

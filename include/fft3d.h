@@ -172,6 +172,41 @@ const char* fft3d_pass_name(int pass);
 double fft3d_pass_bytes(fft3d_handle plan, int pass);
 
 /*
+ * Autotuning.  A plan's kernel shapes (columns per CTA of the n0 and n1
+ * column kernels, rows per CTA of the row kernels, TMA or plain kernel for the
+ * n0 pass) start at compiled defaults; fft3d_autotune times each pass's
+ * candidates on the caller's buffers (real: batch*N floats, cplx: batch*M
+ * float2; both device, contents destroyed) with CUDA events, reps timed runs
+ * per candidate, and keeps the fastest.  Synchronises stream.  The choices
+ * are four ints {w0, w1, rows, tma} (0 = compiled default) that
+ * fft3d_get_choices / fft3d_set_choices read and write (host array), so a
+ * caller can cache them per GPU and shape.
+ */
+int fft3d_autotune(fft3d_handle plan, float* real, void* cplx, int reps, void* stream);
+int fft3d_get_choices(fft3d_handle plan, int* choices4);
+int fft3d_set_choices(fft3d_handle plan, const int* choices4);
+
+/*
+ * Grouped transforms of uneven sizes (e.g. several grids of a multi-resolution
+ * run).  dims: ngroups x 3 ints (n0, n1, n2) (host); counts: fields per group
+ * (host).  Group i is a plan of batch counts[i]; fft3d_group_r2c / c2r take
+ * host arrays of ngroups device pointers (group i's fields contiguous, layouts
+ * as for fft3d_r2c / fft3d_c2r; c2r clobbers its inputs).  The groups run on
+ * internal streams forked from and joined back into stream; on a non-default
+ * stream the whole group is captured once per operand set into a CUDA graph
+ * and replayed with a single graph launch.  fft3d_group_plan_at gives group i's
+ * plan (for fft3d_autotune / fft3d_set_choices; tune before the first call
+ * with a given operand set, since a captured graph keeps the launch shapes).
+ */
+typedef struct fft3d_group_s* fft3d_group_handle;
+fft3d_group_handle fft3d_plan_group(const int* dims, const int* counts, int ngroups, int dtype);
+fft3d_handle fft3d_group_plan_at(fft3d_group_handle group, int i);
+int fft3d_group_r2c(fft3d_group_handle group, const float* const* in, void* const* out, void* stream);
+int fft3d_group_c2r(fft3d_group_handle group, void* const* in, float* const* out, void* stream);
+int fft3d_group_launches(fft3d_group_handle group, int dir);
+void fft3d_group_destroy(fft3d_group_handle group);
+
+/*
  * Pseudo-spectral nonlinear term (the quadratic term of the Tarang-type
  * solvers of Sec. 1; the paper states that FFTs take about 75% of such a
  * solver's time).  For a velocity field given by its three half spectra

@@ -70,6 +70,15 @@ _SIGS = {
     "fft3d_nonlinear_exec": ([_P, _P, _P, _P], _I),
     "fft3d_nonlinear_launches": ([_P], _I),
     "fft3d_nonlinear_destroy": ([_P], None),
+    "fft3d_autotune": ([_P, _P, _P, _I, _P], _I),
+    "fft3d_get_choices": ([_P, _P], _I),
+    "fft3d_set_choices": ([_P, _P], _I),
+    "fft3d_plan_group": ([_P, _P, _I, _I], _P),
+    "fft3d_group_plan_at": ([_P, _I], _P),
+    "fft3d_group_r2c": ([_P, _P, _P, _P], _I),
+    "fft3d_group_c2r": ([_P, _P, _P, _P], _I),
+    "fft3d_group_launches": ([_P, _I], _I),
+    "fft3d_group_destroy": ([_P], None),
 }
 
 
@@ -265,6 +274,91 @@ class NonlinearTerm:
     def close(self):
         if self.handle:
             fft3d_nonlinear_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fft3d_autotune(plan, real_ptr, cplx_ptr, reps=5, stream=0):
+    return load().fft3d_autotune(_v(plan), _v(real_ptr), _v(cplx_ptr), reps, _v(stream))
+
+
+def fft3d_get_choices(plan):
+    c = (ctypes.c_int * 4)()
+    st = load().fft3d_get_choices(_v(plan), c)
+    if st != FFT3D_OK:
+        raise Fft3dError(st, "fft3d_get_choices")
+    return list(c)
+
+
+def fft3d_set_choices(plan, choices):
+    c = (ctypes.c_int * 4)(*choices)
+    return load().fft3d_set_choices(_v(plan), c)
+
+
+def _ptr_array(ptrs):
+    return (ctypes.c_void_p * len(ptrs))(*[int(p) for p in ptrs])
+
+
+def fft3d_plan_group(dims, counts, dtype=FFT3D_F32):
+    d = (ctypes.c_int * (3 * len(dims)))(*[int(v) for t in dims for v in t])
+    c = (ctypes.c_int * len(counts))(*[int(v) for v in counts])
+    return load().fft3d_plan_group(d, c, len(dims), dtype)
+
+
+def fft3d_group_plan_at(group, i):
+    return load().fft3d_group_plan_at(_v(group), i)
+
+
+def fft3d_group_r2c(group, in_ptrs, out_ptrs, stream=0):
+    return load().fft3d_group_r2c(_v(group), _ptr_array(in_ptrs), _ptr_array(out_ptrs), _v(stream))
+
+
+def fft3d_group_c2r(group, in_ptrs, out_ptrs, stream=0):
+    return load().fft3d_group_c2r(_v(group), _ptr_array(in_ptrs), _ptr_array(out_ptrs), _v(stream))
+
+
+def fft3d_group_launches(group, direction=-1):
+    return load().fft3d_group_launches(_v(group), direction)
+
+
+def fft3d_group_destroy(group):
+    load().fft3d_group_destroy(_v(group))
+
+
+class Group:
+    """Owning wrapper of a grouped plan: dims [(n0, n1, n2), ...], counts
+    [fields, ...].  r2c / c2r take lists of torch CUDA tensors, one per group
+    (group i: counts[i] contiguous fields)."""
+
+    def __init__(self, dims, counts, dtype=FFT3D_F32):
+        h = fft3d_plan_group(dims, counts, dtype)
+        if not h:
+            raise Fft3dError(fft3d_last_error(), "fft3d_plan_group")
+        self.handle = h
+        self.dims = [tuple(d) for d in dims]
+        self.counts = list(counts)
+
+    def plan_at(self, i):
+        return fft3d_group_plan_at(self.handle, i)
+
+    def r2c(self, ins, outs, stream=0):
+        st = fft3d_group_r2c(self.handle, [t.data_ptr() for t in ins], [t.data_ptr() for t in outs], stream)
+        if st != FFT3D_OK:
+            raise Fft3dError(st, "fft3d_group_r2c")
+
+    def c2r(self, ins, outs, stream=0):
+        st = fft3d_group_c2r(self.handle, [t.data_ptr() for t in ins], [t.data_ptr() for t in outs], stream)
+        if st != FFT3D_OK:
+            raise Fft3dError(st, "fft3d_group_c2r")
+
+    def close(self):
+        if self.handle:
+            fft3d_group_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -154,6 +154,10 @@ struct fft3d_plan_s {
     int ring_planes = 0;
     double* d_energy = nullptr;         // scratch of fft3d_energy (block partials)
     size_t energy_doubles = 0;
+    // kernel shape choices (autotuner): columns per CTA of the n0 / n1 column
+    // kernels, rows per CTA of the row kernels (0: compiled default), and
+    // whether the n0 pass may use the TMA kernel
+    int choice_w0 = 0, choice_w1 = 0, choice_rows = 0, choice_tma = 1;
     void* workspace = nullptr;
     std::string desc;
     bool profiling = false;
@@ -258,11 +262,13 @@ cudaError_t launch_col_args(fft3d_plan_s* p, const Axis& a, int dir, const ColAr
         if (!ca.dst && ca.scale == 1.0f) return cudaSuccess;
     }
     if (uses_generic(p, a, false)) return generic_col(ca, a.gen, dir, s);
-    if (tma_ok(p, a, ca.S, ca.C, ca.Bs)) {
+    const bool n0axis = (&a == &p->ax0);
+    if ((!n0axis || p->choice_tma) && tma_ok(p, a, ca.S, ca.C, ca.Bs)) {
         if (const CUtensorMap* m = tensor_map(p, a, ca))
             return dir < 0 ? a.spec->tma_fwd(ca, *m, s) : a.spec->tma_inv(ca, *m, s);
     }
-    return dir < 0 ? a.spec->col_fwd(ca, s) : a.spec->col_inv(ca, s);
+    const int w = n0axis ? p->choice_w0 : p->choice_w1;
+    return dir < 0 ? a.spec->col_fwd(ca, w, s) : a.spec->col_inv(ca, w, s);
 }
 
 cudaError_t run_col(fft3d_plan_s* p, const Axis& a, int dir, float2* data, long long S, long long C,
@@ -280,7 +286,7 @@ cudaError_t run_row(fft3d_plan_s* p, int dir, const void* in, void* out, cudaStr
     ProfScope ps(p, dir < 0 ? PASS_ROW_R2C : PASS_ROW_C2R, s);
     RowArgs ra{in, out, (long long)p->batch * p->n0 * p->n1, p->ax2.d_tw, p->d_twpack};
     if (uses_generic(p, p->ax2, true)) return generic_row(ra, p->ax2.gen, dir, s);
-    return dir < 0 ? p->ax2.spec->r2c(ra, s) : p->ax2.spec->c2r(ra, s);
+    return dir < 0 ? p->ax2.spec->r2c(ra, p->choice_rows, s) : p->ax2.spec->c2r(ra, p->choice_rows, s);
 }
 
 std::string axis_desc(const fft3d_plan_s* p, const Axis& a, bool row)
@@ -290,12 +296,17 @@ std::string axis_desc(const fft3d_plan_s* p, const Axis& a, bool row)
     if (uses_generic(p, a, row)) {
         std::snprintf(b, sizeof b, "generic L=%d", a.L);
     } else if (row) {
-        std::snprintf(b, sizeof b, "L=%d E=%d rows/CTA=%d %s", a.L, a.spec->row_E, a.spec->row_rows,
+        const int rr = (p->choice_rows > 0 && p->choice_rows <= a.spec->row_rows && a.spec->row_warp)
+                           ? p->choice_rows
+                           : a.spec->row_rows;
+        std::snprintf(b, sizeof b, "L=%d E=%d rows/CTA=%d %s", a.L, a.spec->row_E, rr,
                       a.spec->row_warp ? "warp" : "smem");
-    } else if (&a == &p->ax0 && a.spec->tma_W && !(p->flags & FFT3D_FLAG_THREE_PASS)) {
+    } else if (&a == &p->ax0 && a.spec->tma_W && !(p->flags & FFT3D_FLAG_THREE_PASS) && p->choice_tma) {
         std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d tma", a.L, a.spec->tma_E, a.spec->tma_W);
     } else {
-        std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d", a.L, a.spec->col_E, a.spec->col_W);
+        const int w = (&a == &p->ax0) ? p->choice_w0 : p->choice_w1;
+        std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d", a.L, a.spec->col_E,
+                      (w > 0 && w <= a.spec->col_W) ? w : a.spec->col_W);
     }
     return b;
 }
@@ -330,6 +341,22 @@ cudaError_t run_swap(fft3d_plan_s* p, const float2* in, float2* out, long long a
 {
     ProfScope ps(p, PASS_SWAP01, s);
     return launch_swap01(in, out, p->batch, a0, a1, p->H, s);
+}
+
+std::string describe_plan(const fft3d_plan_s* p)
+{
+    const int flags = p->flags;
+    std::string d = "rows[" + axis_desc(p, p->ax2, true) + "] n1[" + axis_desc(p, p->ax1, false) + "] n0[" +
+                    axis_desc(p, p->ax0, false) + "]";
+    if (p->plane) {
+        char b[128];
+        std::snprintf(b, sizeof b, "plane[fused rows E=%d + n1 E=%d, %d threads]", p->plane->ER, p->plane->EC,
+                      p->plane->NT);
+        d = std::string(b) + " n0[" + axis_desc(p, p->ax0, false) + "]";
+    }
+    if (flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE)
+        d += (flags & FFT3D_FLAG_TRANSPOSE_BACK) ? " explicit-transpose+back" : " explicit-transpose";
+    return d;
 }
 
 bool overlaps(const void* a, size_t na, const void* b, size_t nb)
@@ -461,17 +488,7 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
             return nullptr;
         }
     }
-    std::string d = "rows[" + axis_desc(p, p->ax2, true) + "] n1[" + axis_desc(p, p->ax1, false) + "] n0[" +
-                    axis_desc(p, p->ax0, false) + "]";
-    if (p->plane) {
-        char b[128];
-        std::snprintf(b, sizeof b, "plane[fused rows E=%d + n1 E=%d, %d threads]", p->plane->ER, p->plane->EC,
-                      p->plane->NT);
-        d = std::string(b) + " n0[" + axis_desc(p, p->ax0, false) + "]";
-    }
-    if (flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE)
-        d += (flags & FFT3D_FLAG_TRANSPOSE_BACK) ? " explicit-transpose+back" : " explicit-transpose";
-    p->desc = d;
+    p->desc = describe_plan(p);
     return p;
 }
 
@@ -505,7 +522,7 @@ int fft3d_set_workspace(fft3d_handle p, void* dev_ptr)
 int fft3d_describe(fft3d_handle p, char* text, int len)
 {
     if (!p || !text || len < 1) return fail(FFT3D_ERR_INVALID_ARG);
-    std::snprintf(text, (size_t)len, "%dx%dx%d batch=%d %s", p->n0, p->n1, p->n2, p->batch, p->desc.c_str());
+    std::snprintf(text, (size_t)len, "%dx%dx%d batch=%d %s", p->n0, p->n1, p->n2, p->batch, describe_plan(p).c_str());
     return FFT3D_OK;
 }
 
@@ -776,6 +793,281 @@ void fft3d_nonlinear_destroy(fft3d_nl_handle nl)
     drop_graph(nl);
     fft3d_destroy(nl->plan);
     delete nl;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner and shape choices.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+template <class F>
+float time_pass(F&& f, int reps, cudaStream_t s)
+{
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    f();  // warm-up (also first-use set-up of the kernel)
+    cudaEventRecord(a, s);
+    for (int i = 0; i < reps; ++i) f();
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return (cudaGetLastError() == cudaSuccess) ? ms / reps : 1e30f;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fft3d_get_choices(fft3d_handle p, int* c)
+{
+    if (!p || !c) return fail(FFT3D_ERR_INVALID_ARG);
+    c[0] = p->choice_w0;
+    c[1] = p->choice_w1;
+    c[2] = p->choice_rows;
+    c[3] = p->choice_tma;
+    return FFT3D_OK;
+}
+
+int fft3d_set_choices(fft3d_handle p, const int* c)
+{
+    if (!p || !c || c[0] < 0 || c[1] < 0 || c[2] < 0 || (c[3] != 0 && c[3] != 1)) return fail(FFT3D_ERR_INVALID_ARG);
+    p->choice_w0 = c[0];
+    p->choice_w1 = c[1];
+    p->choice_rows = c[2];
+    p->choice_tma = c[3];
+    return FFT3D_OK;
+}
+
+int fft3d_autotune(fft3d_handle p, float* real, void* cplx, int reps, void* stream)
+{
+    if (!p || !real || !cplx) return fail(FFT3D_ERR_INVALID_ARG);
+    if (((uintptr_t)real & 15) || ((uintptr_t)cplx & 15)) return fail(FFT3D_ERR_MISALIGNED);
+    if (p->flags & (FFT3D_FLAG_GENERIC | FFT3D_FLAG_EXPLICIT_TRANSPOSE)) return FFT3D_OK;  // nothing to choose
+    if (reps < 1) reps = 5;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool prof = p->profiling;
+    p->profiling = false;
+    const long long H = p->H, n0 = p->n0, n1 = p->n1, B = p->batch;
+    float2* X = (float2*)cplx;
+    // rows per CTA of the row kernels
+    if (p->ax2.spec && p->ax2.spec->row_warp) {
+        const int R = p->ax2.spec->row_rows, T = p->ax2.L / p->ax2.spec->row_E;
+        float best = 1e30f;
+        int pick = 0;
+        for (int r = R; r >= 1; r /= 2) {
+            if ((T * r) % 32) break;
+            p->choice_rows = r;
+            const float t = time_pass([&] { run_row(p, -1, real, X, s); }, reps, s);
+            if (t < best) best = t, pick = r;
+        }
+        p->choice_rows = pick;
+    }
+    // columns per CTA of the n1 pass
+    if (p->ax1.L > 1 && p->ax1.spec) {
+        float best = 1e30f;
+        int pick = 0;
+        for (int w = p->ax1.spec->col_W; w >= 4 && w * 4 >= p->ax1.spec->col_W; w /= 2) {
+            p->choice_w1 = w;
+            const float t = time_pass([&] { run_col(p, p->ax1, -1, X, H, H, B * n0, n1 * H, s); }, reps, s);
+            if (t < best) best = t, pick = w;
+        }
+        p->choice_w1 = pick;
+    }
+    // n0 pass: the TMA kernel or the plain kernel at several widths
+    if (p->ax0.L > 1 && p->ax0.spec) {
+        float best = 1e30f;
+        int pick_w = 0, pick_tma = 0;
+        if (tma_ok(p, p->ax0, p->P, p->P, p->M)) {
+            p->choice_tma = 1;
+            best = time_pass([&] { run_col(p, p->ax0, -1, X, p->P, p->P, B, p->M, s); }, reps, s);
+            pick_tma = 1;
+        }
+        p->choice_tma = 0;
+        for (int w = p->ax0.spec->col_W; w >= 4 && w * 4 >= p->ax0.spec->col_W; w /= 2) {
+            p->choice_w0 = w;
+            const float t = time_pass([&] { run_col(p, p->ax0, -1, X, p->P, p->P, B, p->M, s); }, reps, s);
+            if (t < best) best = t, pick_w = w, pick_tma = 0;
+        }
+        p->choice_w0 = pick_w;
+        p->choice_tma = pick_tma;
+    }
+    p->profiling = prof;
+    return cudaGetLastError() == cudaSuccess ? FFT3D_OK : fail(FFT3D_ERR_CUDA);
+}
+
+// ---------------------------------------------------------------------------
+// Grouped transforms of uneven sizes: one plan per size (its fields form the
+// plan's batch), each size on its own stream, forked from and joined back
+// into the caller's stream; on a non-default stream the whole group is
+// captured once per operand set into a CUDA graph and replayed.
+// ---------------------------------------------------------------------------
+struct fft3d_group_s {
+    std::vector<fft3d_plan_s*> plans;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+    struct Graph {
+        std::vector<const void*> in;
+        std::vector<void*> out;
+        int dir = 0;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+    } graphs[2];  // one per direction
+};
+
+namespace {
+
+void group_free(fft3d_group_s* g)
+{
+    for (auto& gr : g->graphs) {
+        if (gr.exec) cudaGraphExecDestroy(gr.exec);
+        if (gr.graph) cudaGraphDestroy(gr.graph);
+    }
+    for (auto* p : g->plans) fft3d_destroy(p);
+    for (auto st : g->streams) cudaStreamDestroy(st);
+    for (auto e : g->joins) cudaEventDestroy(e);
+    if (g->fork) cudaEventDestroy(g->fork);
+    delete g;
+}
+
+int group_enqueue(fft3d_group_s* g, int dir, const void* const* in, void* const* out, cudaStream_t s)
+{
+    if (cudaEventRecord(g->fork, s) != cudaSuccess) return FFT3D_ERR_CUDA;
+    for (size_t i = 0; i < g->plans.size(); ++i) {
+        if (cudaStreamWaitEvent(g->streams[i], g->fork, 0) != cudaSuccess) return FFT3D_ERR_CUDA;
+        const int st = dir < 0 ? fft3d_r2c(g->plans[i], (const float*)in[i], out[i], g->streams[i])
+                               : fft3d_c2r(g->plans[i], const_cast<void*>(in[i]), (float*)out[i], g->streams[i]);
+        if (st != FFT3D_OK) return st;
+        if (cudaEventRecord(g->joins[i], g->streams[i]) != cudaSuccess) return FFT3D_ERR_CUDA;
+        if (cudaStreamWaitEvent(s, g->joins[i], 0) != cudaSuccess) return FFT3D_ERR_CUDA;
+    }
+    return FFT3D_OK;
+}
+
+int group_exec(fft3d_group_s* g, int dir, const void* const* in, void* const* out, cudaStream_t s)
+{
+    const size_t n = g->plans.size();
+    if (!in || !out) return fail(FFT3D_ERR_INVALID_ARG);
+    for (size_t i = 0; i < n; ++i)
+        if (!in[i] || !out[i]) return fail(FFT3D_ERR_INVALID_ARG);
+    if (!s) {  // the legacy default stream cannot be captured: fork/join directly
+        const int st = group_enqueue(g, dir, in, out, s);
+        return st == FFT3D_OK ? FFT3D_OK : fail(st);
+    }
+    auto& gr = g->graphs[dir < 0 ? 0 : 1];
+    bool same = gr.exec != nullptr && gr.in.size() == n;
+    for (size_t i = 0; same && i < n; ++i) same = gr.in[i] == in[i] && gr.out[i] == out[i];
+    if (!same) {
+        if (gr.exec) cudaGraphExecDestroy(gr.exec);
+        if (gr.graph) cudaGraphDestroy(gr.graph);
+        gr.exec = nullptr;
+        gr.graph = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        const int st = group_enqueue(g, dir, in, out, s);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (st != FFT3D_OK || e != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(st != FFT3D_OK ? st : FFT3D_ERR_CUDA);
+        }
+        gr.graph = graph;
+        if (cudaGraphInstantiate(&gr.exec, graph, 0) != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            gr.graph = nullptr;
+            return fail(FFT3D_ERR_CUDA);
+        }
+        gr.in.assign(in, in + n);
+        gr.out.assign(out, out + n);
+    }
+    return cudaGraphLaunch(gr.exec, s) == cudaSuccess ? FFT3D_OK : fail(FFT3D_ERR_CUDA);
+}
+
+}  // namespace
+
+fft3d_group_handle fft3d_plan_group(const int* dims, const int* counts, int ngroups, int dtype)
+{
+    if (!dims || !counts || ngroups < 1 || ngroups > 64) {
+        fail(FFT3D_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    fft3d_group_s* g = new (std::nothrow) fft3d_group_s();
+    if (!g) {
+        fail(FFT3D_ERR_ALLOC);
+        return nullptr;
+    }
+    for (int i = 0; i < ngroups; ++i) {
+        fft3d_handle p = fft3d_plan(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], dtype, counts[i]);
+        if (!p) {
+            const int st = fft3d_last_error();
+            group_free(g);
+            fail(st);
+            return nullptr;
+        }
+        g->plans.push_back(p);
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            group_free(g);
+            fail(FFT3D_ERR_CUDA);
+            return nullptr;
+        }
+        g->streams.push_back(st);
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            group_free(g);
+            fail(FFT3D_ERR_CUDA);
+            return nullptr;
+        }
+        g->joins.push_back(ev);
+    }
+    if (cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) != cudaSuccess) {
+        group_free(g);
+        fail(FFT3D_ERR_CUDA);
+        return nullptr;
+    }
+    return g;
+}
+
+fft3d_handle fft3d_group_plan_at(fft3d_group_handle g, int i)
+{
+    if (!g || i < 0 || i >= (int)g->plans.size()) {
+        fail(FFT3D_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    return g->plans[(size_t)i];
+}
+
+int fft3d_group_r2c(fft3d_group_handle g, const float* const* in, void* const* out, void* stream)
+{
+    if (!g) return fail(FFT3D_ERR_INVALID_ARG);
+    return group_exec(g, -1, reinterpret_cast<const void* const*>(in), out, (cudaStream_t)stream);
+}
+
+int fft3d_group_c2r(fft3d_group_handle g, void* const* in, float* const* out, void* stream)
+{
+    if (!g) return fail(FFT3D_ERR_INVALID_ARG);
+    return group_exec(g, +1, const_cast<const void* const*>(in), reinterpret_cast<void* const*>(out),
+                      (cudaStream_t)stream);
+}
+
+int fft3d_group_launches(fft3d_group_handle g, int dir)
+{
+    if (!g) return fail(FFT3D_ERR_INVALID_ARG);
+    int n = 0;
+    for (auto* p : g->plans) n += fft3d_launches_per_call(p, dir);
+    return n;
+}
+
+void fft3d_group_destroy(fft3d_group_handle g)
+{
+    if (!g) return;
+    cudaDeviceSynchronize();
+    group_free(g);
 }
 
 int fft3d_set_profiling(fft3d_handle p, int enable)

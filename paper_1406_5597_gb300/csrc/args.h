@@ -48,9 +48,11 @@ struct GenPlan {
     int radix[24];
 };
 
-using ColFn = cudaError_t (*)(const ColArgs&, cudaStream_t);
+// Launchers take a runtime shape choice: w = columns per CTA (0 or > compiled
+// maximum: the compiled value), rows = rows per CTA (same rule).
+using ColFn = cudaError_t (*)(const ColArgs&, int w, cudaStream_t);
 using ColTmaFn = cudaError_t (*)(const ColArgs&, const CUtensorMap&, cudaStream_t);
-using RowFn = cudaError_t (*)(const RowArgs&, cudaStream_t);
+using RowFn = cudaError_t (*)(const RowArgs&, int rows, cudaStream_t);
 struct NlRowArgs {
     const float2* in;
     float2* out;

@@ -348,7 +348,7 @@ __global__ void __launch_bounds__((L / E) * ROWS) row_r2c_warp_kernel(RowArgs a)
     constexpr int T = L / E;
     constexpr int H = L + 1;
     const int t = threadIdx.x, r = threadIdx.y;
-    const long long row = (long long)blockIdx.x * ROWS + r;
+    const long long row = (long long)blockIdx.x * blockDim.y + r;
     row_r2c_body<L, E, false>(reinterpret_cast<const float2*>(a.in) + row * L,
                               reinterpret_cast<float2*>(a.out) + row * H, row < a.rows, t, (r * T + t) & 31,
                               sm + r * RowLayout<L>::stride, a.tw, a.twpack);
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__((L / E) * ROWS) row_c2r_warp_kernel(RowArgs a)
     constexpr int T = L / E;
     constexpr int H = L + 1;
     const int t = threadIdx.x, r = threadIdx.y;
-    const long long row = (long long)blockIdx.x * ROWS + r;
+    const long long row = (long long)blockIdx.x * blockDim.y + r;
     row_c2r_body<L, E, false>(reinterpret_cast<const float2*>(a.in) + row * H,
                               reinterpret_cast<float2*>(a.out) + row * L, row < a.rows, t, (r * T + t) & 31,
                               sm + r * RowLayout<L>::stride, a.tw, a.twpack);
@@ -601,22 +601,24 @@ inline ColShape col_shape()
 }
 
 template <int L, int E, int W, int DIR>
-inline cudaError_t launch_col(const ColArgs& a, cudaStream_t s)
+inline cudaError_t launch_col(const ColArgs& a, int w, cudaStream_t s)
 {
     constexpr int T = L / E;
     constexpr int MAXT = W * T;
     static_assert(MAXT <= 1024, "too many threads");
-    const size_t smem = (size_t)L * W * sizeof(float2);
+    const int wr = (w > 0 && w <= W) ? w : W;  // runtime columns per CTA
+    const size_t smem_max = (size_t)L * W * sizeof(float2);
+    const size_t smem = (size_t)L * wr * sizeof(float2);
     auto k = col_kernel<L, E, DIR, MAXT>;
     static bool attr_set = false;  // one attribute call per instantiation (per process)
-    if (smem > 48 * 1024 && !attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem_max > 48 * 1024 && !attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const long long tiles = a.nb * ((a.C + W - 1) / W);
+    const long long tiles = a.nb * ((a.C + wr - 1) / wr);
     if (tiles <= 0) return cudaSuccess;
-    k<<<(unsigned)tiles, dim3(W, T), smem, s>>>(a, W);
+    k<<<(unsigned)tiles, dim3(wr, T), smem, s>>>(a, wr);
     return cudaGetLastError();
 }
 
@@ -627,7 +629,7 @@ inline size_t row_smem()
 }
 
 template <int L, int E, int ROWS, int DIR>
-inline cudaError_t launch_row(const RowArgs& a, cudaStream_t s)
+inline cudaError_t launch_row(const RowArgs& a, int /*rows: fixed for the staged kernel*/, cudaStream_t s)
 {
     constexpr int T = L / E;
     const size_t smem = row_smem<L, E, ROWS>();
@@ -652,21 +654,24 @@ inline cudaError_t launch_row(const RowArgs& a, cudaStream_t s)
 }
 
 template <int L, int E, int ROWS, int DIR>
-inline cudaError_t launch_row_warp(const RowArgs& a, cudaStream_t s)
+inline cudaError_t launch_row_warp(const RowArgs& a, int rows, cudaStream_t s)
 {
     constexpr int T = L / E;
     static_assert((T * ROWS) % 32 == 0, "the shuffles need whole warps");
-    const size_t smem = (num_stages(L, E) > 1) ? row_smem<L, E, ROWS>() : 0;
-    const long long blocks = (a.rows + ROWS - 1) / ROWS;
+    // runtime rows per CTA: at most ROWS, whole warps
+    const int rr = (rows > 0 && rows <= ROWS && (T * rows) % 32 == 0) ? rows : ROWS;
+    const size_t smem_max = (num_stages(L, E) > 1) ? row_smem<L, E, ROWS>() : 0;
+    const size_t smem = smem_max / ROWS * rr;
+    const long long blocks = (a.rows + rr - 1) / rr;
     if (blocks <= 0) return cudaSuccess;
     auto k = (DIR < 0) ? row_r2c_warp_kernel<L, E, ROWS> : row_c2r_warp_kernel<L, E, ROWS>;
     static bool attr_set = false;
-    if (smem > 48 * 1024 && !attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem_max > 48 * 1024 && !attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k<<<(unsigned)blocks, dim3(T, ROWS), smem, s>>>(a);
+    k<<<(unsigned)blocks, dim3(T, rr), smem, s>>>(a);
     return cudaGetLastError();
 }
 

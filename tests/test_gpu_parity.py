@@ -330,6 +330,84 @@ def test_nonlinear_term_recaptures_for_new_buffers(cuda_lib):
 
 
 # ---------------------------------------------------------------------------
+# Grouped uneven batch (64^3, 96^3, 128^3, 192^3, 160^3 x 4 fields) and the
+# autotuner.
+# ---------------------------------------------------------------------------
+GROUP_DIMS = [(64, 64, 64), (96, 96, 96), (128, 128, 128), (192, 192, 192), (160, 160, 160)]
+
+
+def test_grouped_uneven_batch_matches_oracle(cuda_lib):
+    lib = cuda_lib
+    counts = [4] * len(GROUP_DIMS)
+    g = lib.Group(GROUP_DIMS, counts)
+    xs, Xs, refs = [], [], []
+    for i, (n0, n1, n2) in enumerate(GROUP_DIMS):
+        x32 = synth.uniform_field((4, n0, n1, n2), seed=synth.seed_for_config(4, field=i + 1)).astype(np.float32)
+        xs.append(torch.from_numpy(x32).cuda())
+        Xs.append(torch.empty((4, n0, n1, n2 // 2 + 1), dtype=torch.complex64, device="cuda"))
+        refs.append(x32)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        g.r2c(xs, Xs, stream=s.cuda_stream)   # captured into one graph
+        g.r2c(xs, Xs, stream=s.cuda_stream)   # replayed
+    s.synchronize()
+    for i, (n0, n1, n2) in enumerate(GROUP_DIMS):
+        got = Xs[i].cpu().numpy().astype(np.complex128)
+        for f in (0, 3):
+            assert rel_l2(got[f], oracle.r2c3d(refs[i][f].astype(np.float64))) <= TOL
+    # inverse on the legacy default stream (direct fork/join), inputs clobbered
+    Ys = [X.clone() for X in Xs]
+    outs = [torch.empty_like(x) for x in xs]
+    g.c2r(Ys, outs, stream=0)
+    torch.cuda.synchronize()
+    for i, (n0, n1, n2) in enumerate(GROUP_DIMS):
+        N = n0 * n1 * n2
+        y = outs[i].cpu().numpy().astype(np.float64)
+        for f in (1, 2):
+            assert rel_l2(y[f] / N, refs[i][f].astype(np.float64)) <= TOL_RT
+    assert lib.fft3d_group_launches(g.handle, -1) == 15
+    g.close()
+
+
+def test_autotune_keeps_parity_and_choices_roundtrip(cuda_lib):
+    lib = cuda_lib
+    n0, n1, n2 = 256, 96, 128
+    plan = lib.Plan(n0, n1, n2)
+    real = torch.randn(n0 * n1 * n2, device="cuda")
+    cplx = torch.empty(n0 * n1 * (n2 // 2 + 1), dtype=torch.complex64, device="cuda")
+    assert lib.fft3d_autotune(plan.handle, real.data_ptr(), cplx.data_ptr(), 2) == lib.FFT3D_OK
+    ch = lib.fft3d_get_choices(plan.handle)
+    assert len(ch) == 4 and ch[3] in (0, 1)
+    x32 = synth.uniform_field((n0, n1, n2), seed=91).astype(np.float32)
+    xd = torch.from_numpy(x32).cuda()
+    X = torch.empty((n0, n1, n2 // 2 + 1), dtype=torch.complex64, device="cuda")
+    plan.r2c(xd.data_ptr(), X.data_ptr())
+    assert rel_l2(X.cpu().numpy(), oracle.r2c3d(x32.astype(np.float64))) <= TOL
+    # every candidate shape gives the same transform
+    for choice in ([0, 0, 0, 1], [4, 8, 2, 0], [8, 16, 4, 0]):
+        assert lib.fft3d_set_choices(plan.handle, choice) == lib.FFT3D_OK
+        assert lib.fft3d_get_choices(plan.handle) == choice
+        plan.r2c(xd.data_ptr(), X.data_ptr())
+        assert rel_l2(X.cpu().numpy(), oracle.r2c3d(x32.astype(np.float64))) <= TOL
+        Y = X.clone()
+        y = torch.empty_like(xd)
+        plan.c2r(Y.data_ptr(), y.data_ptr())
+        assert rel_l2(y.cpu().numpy() / (n0 * n1 * n2), x32.astype(np.float64)) <= TOL_RT
+    assert lib.fft3d_set_choices(plan.handle, [0, 0, 0, 2]) == lib.FFT3D_ERR_INVALID_ARG
+
+
+def test_tuned_plan_uses_the_cache(cuda_lib, tmp_path):
+    from paper_1406_5597_gb300 import tune
+    path = str(tmp_path / "wisdom.json")
+    p1, tuned = tune.tuned_plan(64, 48, 40, path=path, reps=1)
+    assert tuned
+    p2, tuned2 = tune.tuned_plan(64, 48, 40, path=path, reps=1)
+    assert not tuned2
+    assert cuda_lib.fft3d_get_choices(p1.handle) == cuda_lib.fft3d_get_choices(p2.handle)
+
+
+# ---------------------------------------------------------------------------
 # FP64 device diagnostics: Parseval sum and shell energies vs the oracle.
 # ---------------------------------------------------------------------------
 
