@@ -317,6 +317,36 @@ def main():
             vp.close()
         line["variants"] = variants
 
+    # tensor-core radix-16 forms (split-BF16 x3, FP16) of the same step, with
+    # their accuracy against the exact spectrum N*S of the field (x = c2r(S))
+    if not args.no_variants:
+        Sd = torch.from_numpy(S).to(dev)
+        Nn = float(n) ** 3
+
+        def rel_vs_exact(Xc):
+            d = Xc.to(torch.complex128) - Nn * Sd.to(torch.complex128)
+            return float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(Nn * Sd.to(torch.complex128)))
+
+        plan.r2c(x.data_ptr(), X.data_ptr(), sptr)
+        tc = {"fp32": {"ms_per_step": ms, "rel_l2_r2c_vs_exact": rel_vs_exact(X)}}
+        for name, dt in (("tc_bf16x3", fft3d.FFT3D_F32_TC_BF16X3), ("tc_f16", fft3d.FFT3D_F32_TC_F16)):
+            tp = fft3d.Plan(n, n, n, dtype=dt)
+            tp.r2c(x.data_ptr(), X.data_ptr(), sptr)
+            err = rel_vs_exact(X)
+
+            def tstep(tp=tp):
+                tp.r2c(x.data_ptr(), X.data_ptr(), sptr)
+                tp.c2r(X.data_ptr(), y.data_ptr(), sptr)
+
+            for _ in range(3):
+                tstep()
+            tms = time_steps(tstep, stream, max(5, args.steps // 2)) / max(5, args.steps // 2)
+            tc[name] = {"ms_per_step": tms, "gbs_effective": nbytes / (tms * 1e-3) / 1e9,
+                        "rel_l2_r2c_vs_exact": err, "speed_vs_fp32": ms / tms, "plan": tp.describe()}
+            tp.close()
+        line["tensor_core_forms"] = tc
+        del Sd
+
     # pseudo-spectral nonlinear term at 256^3 (3 velocity spectra in, 6 dealiased
     # product spectra out), replayed as one CUDA graph
     if not args.no_variants:

@@ -17,6 +17,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "args.h"
 #include "energy.h"
 #include "fft3d.h"
@@ -125,9 +128,53 @@ GenPlan generic_radices(int L)
 struct Axis {
     int L = 1;
     const LenEntry* spec = nullptr;
+    const TcEntry* tc = nullptr;  // tensor-core radix-16 column kernel (TC dtypes)
     GenPlan gen{};
     float2* d_tw = nullptr;
 };
+
+const TcEntry* find_tc(int L)
+{
+    int n = 0;
+    const TcEntry* e = tc_entries(&n);
+    for (int i = 0; i < n; ++i)
+        if (e[i].L == L) return &e[i];
+    return nullptr;
+}
+
+// Operand tables of the tensor-core radix-16 stages: the real 32 x 32 form of
+// the 16-point DFT, G = [[Fr, -Fi], [Fi, Fr]] (F = exp(-+2 pi i n k / 16)),
+// stored n-major, as 16-bit values: [fwd hi][fwd lo][inv hi][inv lo] with
+// hi = bf16(G), lo = bf16(G - hi) computed from FP64 (split-BF16), or
+// [fwd][0][inv][0] in FP16.
+std::vector<uint16_t> tc_table(int dtype)
+{
+    std::vector<uint16_t> t(4 * 1024, 0);
+    for (int dir = 0; dir < 2; ++dir) {
+        const double sgn = dir == 0 ? -1.0 : 1.0;
+        for (int n = 0; n < 32; ++n)
+            for (int k = 0; k < 32; ++k) {
+                double c, s;
+                root_of_unity((long long)(n % 16) * (k % 16), 16, &c, &s);  // exp(+2 pi i nk/16)
+                const double fr = c, fi = sgn * s;                          // F = fr + i fi
+                double g;
+                if (n < 16) g = (k < 16) ? fr : -fi;
+                else g = (k < 16) ? fi : fr;
+                uint16_t* hi = &t[(size_t)dir * 2048 + (size_t)n * 32 + k];
+                uint16_t* lo = hi + 1024;
+                if (dtype == FFT3D_F32_TC_BF16X3) {
+                    const __nv_bfloat16 h = __float2bfloat16_rn((float)g);
+                    const __nv_bfloat16 l = __float2bfloat16_rn((float)(g - (double)__bfloat162float(h)));
+                    *hi = __bfloat16_as_ushort(h);
+                    *lo = __bfloat16_as_ushort(l);
+                } else {
+                    *hi = __half_as_ushort(__float2half_rn((float)g));
+                    *lo = 0;
+                }
+            }
+    }
+    return t;
+}
 
 }  // namespace
 
@@ -149,6 +196,7 @@ struct fft3d_plan_s {
     float2* d_twpack = nullptr;
     int* d_status = nullptr;
     const PlaneEntry* plane = nullptr;  // fused n2+n1 kernel, when one fits this shape
+    uint16_t* d_tcg = nullptr;          // tensor-core DFT operand table (TC dtypes)
     int* d_counters = nullptr;          // per-plane completion counters + work ticket of the fused kernel
     float2* d_ring = nullptr;           // inverse fused kernel: L2-resident ring of n1-transformed planes
     int ring_planes = 0;
@@ -196,6 +244,7 @@ void free_plan(fft3d_plan_s* p)
     cudaFree(p->d_counters);
     cudaFree(p->d_ring);
     cudaFree(p->d_energy);
+    cudaFree(p->d_tcg);
     delete p;
 }
 
@@ -261,6 +310,11 @@ cudaError_t launch_col_args(fft3d_plan_s* p, const Axis& a, int dir, const ColAr
     if (a.L <= 1) {  // length-1 axis: the transform is the identity (apart from scale / mask / destination)
         if (!ca.dst && ca.scale == 1.0f) return cudaSuccess;
     }
+    if (a.tc) {  // tensor-core radix-16 stages
+        if (p->dtype == FFT3D_F32_TC_BF16X3)
+            return dir < 0 ? a.tc->bf16_fwd(ca, p->d_tcg, s) : a.tc->bf16_inv(ca, p->d_tcg, s);
+        return dir < 0 ? a.tc->f16_fwd(ca, p->d_tcg, s) : a.tc->f16_inv(ca, p->d_tcg, s);
+    }
     if (uses_generic(p, a, false)) return generic_col(ca, a.gen, dir, s);
     const bool n0axis = (&a == &p->ax0);
     if ((!n0axis || p->choice_tma) && tma_ok(p, a, ca.S, ca.C, ca.Bs)) {
@@ -293,6 +347,11 @@ std::string axis_desc(const fft3d_plan_s* p, const Axis& a, bool row)
 {
     char b[96];
     if (a.L <= 1) return "skip";
+    if (!row && a.tc) {
+        std::snprintf(b, sizeof b, "L=%d E=16 cols/CTA=%d tensor-core radix-16 %s", a.L, a.tc->W,
+                      p->dtype == FFT3D_F32_TC_BF16X3 ? "split-bf16x3" : "fp16");
+        return b;
+    }
     if (uses_generic(p, a, row)) {
         std::snprintf(b, sizeof b, "generic L=%d", a.L);
     } else if (row) {
@@ -400,8 +459,8 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
         fail(FFT3D_ERR_UNSUPPORTED_SIZE);
         return nullptr;
     }
-    if (dtype != FFT3D_F32) {  // tensor-core forms are planned separately
-        fail(FFT3D_ERR_UNSUPPORTED_SIZE);
+    if (dtype != FFT3D_F32 && (flags & (FFT3D_FLAG_EXPLICIT_TRANSPOSE | FFT3D_FLAG_GENERIC | FFT3D_FLAG_FUSED_PLANE))) {
+        fail(FFT3D_ERR_INVALID_ARG);  // the tensor-core forms use the plain transpose-free pass sequence
         return nullptr;
     }
     fft3d_plan_s* p = new (std::nothrow) fft3d_plan_s();
@@ -430,6 +489,7 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
         Axis& a = *axes[i];
         a.L = lens[i];
         a.spec = find_len(a.L);
+        a.tc = (dtype != FFT3D_F32 && i < 2) ? find_tc(a.L) : nullptr;
         a.gen = generic_radices(a.L);
         if (a.L >= 1) {
             if (upload(forward_table(a.L, a.L), &a.d_tw) != cudaSuccess) {
@@ -437,6 +497,20 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
                 fail(FFT3D_ERR_ALLOC);
                 return nullptr;
             }
+        }
+    }
+    if (dtype != FFT3D_F32) {
+        if (!p->ax0.tc && !p->ax1.tc) {  // no axis with a tensor-core kernel: the form does not exist here
+            free_plan(p);
+            fail(FFT3D_ERR_UNSUPPORTED_SIZE);
+            return nullptr;
+        }
+        const std::vector<uint16_t> t = tc_table(dtype);
+        if (cudaMalloc((void**)&p->d_tcg, t.size() * sizeof(uint16_t)) != cudaSuccess ||
+            cudaMemcpy(p->d_tcg, t.data(), t.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+            free_plan(p);
+            fail(FFT3D_ERR_ALLOC);
+            return nullptr;
         }
     }
     if (upload(forward_table(n2, n2 / 2 + 1), &p->d_twpack) != cudaSuccess ||
@@ -869,7 +943,7 @@ int fft3d_autotune(fft3d_handle p, float* real, void* cplx, int reps, void* stre
         p->choice_rows = pick;
     }
     // columns per CTA of the n1 pass
-    if (p->ax1.L > 1 && p->ax1.spec) {
+    if (p->ax1.L > 1 && p->ax1.spec && !p->ax1.tc) {
         float best = 1e30f;
         int pick = 0;
         for (int w = p->ax1.spec->col_W; w >= 4 && w * 4 >= p->ax1.spec->col_W; w /= 2) {
@@ -880,7 +954,7 @@ int fft3d_autotune(fft3d_handle p, float* real, void* cplx, int reps, void* stre
         p->choice_w1 = pick;
     }
     // n0 pass: the TMA kernel or the plain kernel at several widths
-    if (p->ax0.L > 1 && p->ax0.spec) {
+    if (p->ax0.L > 1 && p->ax0.spec && !p->ax0.tc) {
         float best = 1e30f;
         int pick_w = 0, pick_tma = 0;
         if (tma_ok(p, p->ax0, p->P, p->P, p->M)) {

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <cstdint>
 
 namespace fft3d {
 
@@ -90,6 +91,14 @@ struct PlaneEntry {
     PlaneFn fwd, inv;
 };
 const PlaneEntry* plane_entries(int* n);
+
+// Column kernels with radix-16 stages on the tensor cores.
+using ColTcFn = cudaError_t (*)(const ColArgs&, const uint16_t* gtab, cudaStream_t);
+struct TcEntry {
+    int L, W;
+    ColTcFn bf16_fwd, bf16_inv, f16_fwd, f16_inv;
+};
+const TcEntry* tc_entries(int* n);
 
 // Generic kernels: dir = -1 forward, +1 inverse.
 cudaError_t generic_col(const ColArgs& a, const GenPlan& g, int dir, cudaStream_t s);

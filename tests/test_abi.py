@@ -41,6 +41,8 @@ def test_plan_rejects_bad_sizes_before_touching_the_device(lib, dims, status):
 
 
 def test_plan_rejects_bad_dtype_batch_flags(lib):
+    assert not fft3d.fft3d_plan(8, 8, 8, 3, 1)
+    assert fft3d.fft3d_last_error() == fft3d.FFT3D_ERR_INVALID_ARG
     assert not fft3d.fft3d_plan(8, 8, 8, 7, 1)
     assert fft3d.fft3d_last_error() == fft3d.FFT3D_ERR_INVALID_ARG
     assert not fft3d.fft3d_plan(8, 8, 8, 0, 0)

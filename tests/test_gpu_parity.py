@@ -330,6 +330,63 @@ def test_nonlinear_term_recaptures_for_new_buffers(cuda_lib):
 
 
 # ---------------------------------------------------------------------------
+# Tensor-core radix-16 forms: split-BF16 (3 products) <= 1e-5, FP16 <= 3e-3.
+# ---------------------------------------------------------------------------
+TC_TOL = {1: 1e-5, 2: 3e-3}
+
+
+def gpu_r2c_dtype(lib, x32, dtype):
+    n0, n1, n2 = x32.shape[-3:]
+    b = 1 if x32.ndim == 3 else x32.shape[0]
+    plan = lib.Plan(n0, n1, n2, dtype, b)
+    xd = torch.from_numpy(np.ascontiguousarray(x32)).cuda()
+    out = torch.empty(x32.shape[:-1] + (n2 // 2 + 1,), dtype=torch.complex64, device="cuda")
+    plan.r2c(xd.data_ptr(), out.data_ptr())
+    torch.cuda.synchronize()
+    assert lib.fft3d_query_device_status(plan.handle) == lib.FFT3D_OK
+    return out.cpu().numpy().astype(np.complex128), plan.describe()
+
+
+def gpu_c2r_dtype(lib, Y64, n2, dtype):
+    n0, n1 = Y64.shape[-3], Y64.shape[-2]
+    b = 1 if Y64.ndim == 3 else Y64.shape[0]
+    plan = lib.Plan(n0, n1, n2, dtype, b)
+    Yd = torch.from_numpy(np.ascontiguousarray(Y64)).cuda()
+    out = torch.empty(Y64.shape[:-3] + (n0, n1, n2), dtype=torch.float32, device="cuda")
+    plan.c2r(Yd.data_ptr(), out.data_ptr())
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("dtype", [1, 2], ids=["bf16x3", "fp16"])
+@pytest.mark.parametrize("shape", [(256, 256, 32), (512, 64, 16), (32, 512, 16), (1024, 16, 8), (2048, 4, 6),
+                                   (256, 24, 20)], ids=lambda s: "x".join(map(str, s)) if isinstance(s, tuple) else s)
+def test_tensor_core_forms_match_oracle(cuda_lib, shape, dtype):
+    n0, n1, n2 = shape
+    x32 = synth.uniform_field(shape, seed=101).astype(np.float32)
+    X, desc = gpu_r2c_dtype(cuda_lib, x32, dtype)
+    assert "tensor-core" in desc
+    err = rel_l2(X, oracle.r2c3d(x32.astype(np.float64)))
+    assert err <= TC_TOL[dtype], err
+    Y = random_half_spectrum((n0, n1, n2 // 2 + 1), seed=103)
+    y = gpu_c2r_dtype(cuda_lib, Y, n2, dtype)
+    err = rel_l2(y, oracle.c2r3d(Y.astype(np.complex128), n2))
+    assert err <= TC_TOL[dtype], err
+
+
+def test_tensor_core_form_batched_and_unsupported(cuda_lib):
+    lib = cuda_lib
+    x32 = synth.uniform_field((2, 256, 8, 12), seed=105).astype(np.float32)
+    X, _ = gpu_r2c_dtype(lib, x32, 1)
+    for b in range(2):
+        assert rel_l2(X[b], oracle.r2c3d(x32[b].astype(np.float64))) <= TC_TOL[1]
+    # no axis of length 256..2048 with a tensor-core kernel: the form is not offered
+    assert not lib.fft3d_plan(32, 32, 32, 1, 1)
+    assert lib.fft3d_last_error() == lib.FFT3D_ERR_UNSUPPORTED_SIZE
+    assert not lib.fft3d_plan_variant(256, 8, 8, 1, 1, lib.FFT3D_FLAG_EXPLICIT_TRANSPOSE)
+
+
+# ---------------------------------------------------------------------------
 # Grouped uneven batch (64^3, 96^3, 128^3, 192^3, 160^3 x 4 fields) and the
 # autotuner.
 # ---------------------------------------------------------------------------
@@ -455,6 +512,15 @@ def field512():
     S = synth.spectral_velocity(n, n, n, seed=synth.seed_for_config(2), components=(0,))[0]
     x = oracle.c2r3d(S, n)
     return S, x
+
+
+@pytest.mark.parametrize("dtype", [1, 2], ids=["bf16x3", "fp16"])
+def test_512_tensor_core_forms(cuda_lib, field512, dtype):
+    S, x = field512
+    n = 512
+    X, desc = gpu_r2c_dtype(cuda_lib, x.astype(np.float32), dtype)
+    assert "tensor-core" in desc
+    assert rel_l2(X, n ** 3 * S) <= TC_TOL[dtype]
 
 
 @pytest.mark.parametrize("flags", [0, 1, 3], ids=["transpose-free", "explicit-transpose", "transpose-back"])
