@@ -71,7 +71,8 @@ typedef enum {
 /* Plan flags for fft3d_plan_variant. */
 #define FFT3D_FLAG_EXPLICIT_TRANSPOSE 0x1 /* comparator: materialise the n0<->n1 transpose (Sec. 2.1, step 2) */
 #define FFT3D_FLAG_TRANSPOSE_BACK 0x2     /* with EXPLICIT_TRANSPOSE: transpose back to n0 x n1 x H */
-#define FFT3D_FLAG_THREE_PASS 0x4         /* force separate n2-row, n1-column and n0-column passes (default) */
+#define FFT3D_FLAG_THREE_PASS 0x4         /* separate n2-row, n1-column and n0-column passes (the default;
+                                             overrides FFT3D_FLAG_FUSED_PLANE) */
 #define FFT3D_FLAG_GENERIC 0x8            /* force the runtime-length kernels (testing) */
 #define FFT3D_FLAG_FUSED_PLANE 0x20       /* fuse the n2-row and n1-column passes into one persistent
                                              kernel that keeps each plane in L2 between its halves
@@ -173,18 +174,18 @@ double fft3d_pass_bytes(fft3d_handle plan, int pass);
 
 /*
  * Autotuning.  A plan's kernel shapes (columns per CTA of the n0 and n1
- * column kernels, rows per CTA of the row kernels, TMA or plain kernel for the
- * n0 pass) start at compiled defaults; fft3d_autotune times each pass's
- * candidates on the caller's buffers (real: batch*N floats, cplx: batch*M
- * float2; both device, contents destroyed) with CUDA events, reps timed runs
- * per candidate, and keeps the fastest.  Synchronises stream.  The choices
- * are four ints {w0, w1, rows, tma} (0 = compiled default) that
- * fft3d_get_choices / fft3d_set_choices read and write (host array), so a
- * caller can cache them per GPU and shape.
+ * column kernels, rows per CTA of the row kernels, TMA-fed or plain kernel for
+ * the n0 and the n1 pass) start at compiled defaults; fft3d_autotune times
+ * each pass's candidates on the caller's buffers (real: batch*N floats, cplx:
+ * batch*M float2; both device, contents destroyed) with CUDA events, reps
+ * timed runs per candidate, and keeps the fastest.  Synchronises stream.  The
+ * choices are five ints {w0, w1, rows, tma0, tma1} (widths/rows 0 = compiled
+ * default; tma flags 0/1) that fft3d_get_choices / fft3d_set_choices read and
+ * write (host array), so a caller can cache them per GPU and shape.
  */
 int fft3d_autotune(fft3d_handle plan, float* real, void* cplx, int reps, void* stream);
-int fft3d_get_choices(fft3d_handle plan, int* choices4);
-int fft3d_set_choices(fft3d_handle plan, const int* choices4);
+int fft3d_get_choices(fft3d_handle plan, int* choices5);
+int fft3d_set_choices(fft3d_handle plan, const int* choices5);
 
 /*
  * Grouped transforms of uneven sizes (e.g. several grids of a multi-resolution

@@ -288,7 +288,7 @@ def fft3d_autotune(plan, real_ptr, cplx_ptr, reps=5, stream=0):
 
 
 def fft3d_get_choices(plan):
-    c = (ctypes.c_int * 4)()
+    c = (ctypes.c_int * 5)()
     st = load().fft3d_get_choices(_v(plan), c)
     if st != FFT3D_OK:
         raise Fft3dError(st, "fft3d_get_choices")
@@ -296,7 +296,9 @@ def fft3d_get_choices(plan):
 
 
 def fft3d_set_choices(plan, choices):
-    c = (ctypes.c_int * 4)(*choices)
+    if len(choices) != 5:
+        raise ValueError("five choices: w0, w1, rows, tma0, tma1")
+    c = (ctypes.c_int * 5)(*choices)
     return load().fft3d_set_choices(_v(plan), c)
 
 

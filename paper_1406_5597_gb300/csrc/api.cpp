@@ -205,7 +205,7 @@ struct fft3d_plan_s {
     // kernel shape choices (autotuner): columns per CTA of the n0 / n1 column
     // kernels, rows per CTA of the row kernels (0: compiled default), and
     // whether the n0 pass may use the TMA kernel
-    int choice_w0 = 0, choice_w1 = 0, choice_rows = 0, choice_tma = 1;
+    int choice_w0 = 0, choice_w1 = 0, choice_rows = 0, choice_tma = 1, choice_tma1 = 1;
     void* workspace = nullptr;
     std::string desc;
     bool profiling = false;
@@ -215,6 +215,7 @@ struct fft3d_plan_s {
     struct MapCache {
         const void* base = nullptr;
         long long S = 0, C = 0, nb = 0;
+        bool pair = false;
         CUtensorMap map;
     } maps[8];
     int next_map = 0;
@@ -279,21 +280,30 @@ bool uses_generic(const fft3d_plan_s* p, const Axis& a, bool row)
 }
 
 // The TMA column kernel needs a 2D tensor view: batch entries stacked as rows
-// (Bs == L*S), row byte stride 8*S a multiple of 16, C*8 rows of at least one box.
-bool tma_ok(const fft3d_plan_s* p, const Axis& a, long long S, long long C, long long Bs)
+// (Bs == L*S) and at least one tile of columns; an even S gives a row stride
+// that is a multiple of 16 bytes, an odd S is handled by the row-pair view
+// (needs an even L).  Returns 0 (no TMA), 1 (rows) or 2 (row pairs).
+int tma_mode(const fft3d_plan_s* p, const Axis& a, long long S, long long C, long long Bs)
 {
-    if (p->flags & (FFT3D_FLAG_GENERIC | FFT3D_FLAG_THREE_PASS)) return false;
-    if (!a.spec || !a.spec->tma_W) return false;
-    return Bs == (long long)a.L * S && (S % 2) == 0 && C >= a.spec->tma_W;
+    if (p->flags & FFT3D_FLAG_GENERIC) return 0;
+    if (!a.spec || !a.spec->tma_W) return 0;
+    if (Bs != (long long)a.L * S || C < a.spec->tma_W) return 0;
+    if (S % 2 == 0) return 1;
+    return (a.L % 2 == 0 && a.spec->tma_pair_fwd) ? 2 : 0;
 }
 
-const CUtensorMap* tensor_map(fft3d_plan_s* p, const Axis& a, const ColArgs& ca)
+bool tma_ok(const fft3d_plan_s* p, const Axis& a, long long S, long long C, long long Bs)
+{
+    return tma_mode(p, a, S, C, Bs) != 0;
+}
+
+const CUtensorMap* tensor_map(fft3d_plan_s* p, const Axis& a, const ColArgs& ca, bool pair)
 {
     for (auto& m : p->maps)
-        if (m.base == ca.data && m.S == ca.S && m.C == ca.C && m.nb == ca.nb) return &m.map;
+        if (m.base == ca.data && m.S == ca.S && m.C == ca.C && m.nb == ca.nb && m.pair == pair) return &m.map;
     auto& m = p->maps[p->next_map];
     p->next_map = (p->next_map + 1) % 8;
-    if (col_tensor_map_host(&m.map, ca, a.L, a.spec->tma_W) != cudaSuccess) {
+    if (col_tensor_map_host(&m.map, ca, a.L, a.spec->tma_W, pair) != cudaSuccess) {
         m.base = nullptr;
         return nullptr;
     }
@@ -301,6 +311,7 @@ const CUtensorMap* tensor_map(fft3d_plan_s* p, const Axis& a, const ColArgs& ca)
     m.S = ca.S;
     m.C = ca.C;
     m.nb = ca.nb;
+    m.pair = pair;
     return &m.map;
 }
 
@@ -317,9 +328,12 @@ cudaError_t launch_col_args(fft3d_plan_s* p, const Axis& a, int dir, const ColAr
     }
     if (uses_generic(p, a, false)) return generic_col(ca, a.gen, dir, s);
     const bool n0axis = (&a == &p->ax0);
-    if ((!n0axis || p->choice_tma) && tma_ok(p, a, ca.S, ca.C, ca.Bs)) {
-        if (const CUtensorMap* m = tensor_map(p, a, ca))
+    const int mode = tma_mode(p, a, ca.S, ca.C, ca.Bs);
+    if ((n0axis ? p->choice_tma : p->choice_tma1) && mode) {
+        if (const CUtensorMap* m = tensor_map(p, a, ca, mode == 2)) {
+            if (mode == 2) return dir < 0 ? a.spec->tma_pair_fwd(ca, *m, s) : a.spec->tma_pair_inv(ca, *m, s);
             return dir < 0 ? a.spec->tma_fwd(ca, *m, s) : a.spec->tma_inv(ca, *m, s);
+        }
     }
     const int w = n0axis ? p->choice_w0 : p->choice_w1;
     return dir < 0 ? a.spec->col_fwd(ca, w, s) : a.spec->col_inv(ca, w, s);
@@ -360,8 +374,11 @@ std::string axis_desc(const fft3d_plan_s* p, const Axis& a, bool row)
                            : a.spec->row_rows;
         std::snprintf(b, sizeof b, "L=%d E=%d rows/CTA=%d %s", a.L, a.spec->row_E, rr,
                       a.spec->row_warp ? "warp" : "smem");
-    } else if (&a == &p->ax0 && a.spec->tma_W && !(p->flags & FFT3D_FLAG_THREE_PASS) && p->choice_tma) {
-        std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d tma", a.L, a.spec->tma_E, a.spec->tma_W);
+    } else if (const int mode = (&a == &p->ax0) ? (p->choice_tma ? tma_mode(p, a, p->P, p->P, p->M) : 0)
+                                                : (p->choice_tma1 ? tma_mode(p, a, p->H, p->H, (long long)p->n1 * p->H)
+                                                                  : 0)) {
+        std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d %s", a.L, a.spec->tma_E, a.spec->tma_W,
+                      mode == 2 ? "tma-row-pairs" : "tma");
     } else {
         const int w = (&a == &p->ax0) ? p->choice_w0 : p->choice_w1;
         std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d", a.L, a.spec->col_E,
@@ -905,16 +922,19 @@ int fft3d_get_choices(fft3d_handle p, int* c)
     c[1] = p->choice_w1;
     c[2] = p->choice_rows;
     c[3] = p->choice_tma;
+    c[4] = p->choice_tma1;
     return FFT3D_OK;
 }
 
 int fft3d_set_choices(fft3d_handle p, const int* c)
 {
-    if (!p || !c || c[0] < 0 || c[1] < 0 || c[2] < 0 || (c[3] != 0 && c[3] != 1)) return fail(FFT3D_ERR_INVALID_ARG);
+    if (!p || !c || c[0] < 0 || c[1] < 0 || c[2] < 0 || (c[3] != 0 && c[3] != 1) || (c[4] != 0 && c[4] != 1))
+        return fail(FFT3D_ERR_INVALID_ARG);
     p->choice_w0 = c[0];
     p->choice_w1 = c[1];
     p->choice_rows = c[2];
     p->choice_tma = c[3];
+    p->choice_tma1 = c[4];
     return FFT3D_OK;
 }
 
@@ -942,16 +962,23 @@ int fft3d_autotune(fft3d_handle p, float* real, void* cplx, int reps, void* stre
         }
         p->choice_rows = pick;
     }
-    // columns per CTA of the n1 pass
+    // n1 pass: the TMA kernel (rows or row pairs) or the plain kernel at several widths
     if (p->ax1.L > 1 && p->ax1.spec && !p->ax1.tc) {
         float best = 1e30f;
-        int pick = 0;
+        int pick = 0, pick_tma = 0;
+        if (tma_ok(p, p->ax1, H, H, n1 * H)) {
+            p->choice_tma1 = 1;
+            best = time_pass([&] { run_col(p, p->ax1, -1, X, H, H, B * n0, n1 * H, s); }, reps, s);
+            pick_tma = 1;
+        }
+        p->choice_tma1 = 0;
         for (int w = p->ax1.spec->col_W; w >= 4 && w * 4 >= p->ax1.spec->col_W; w /= 2) {
             p->choice_w1 = w;
             const float t = time_pass([&] { run_col(p, p->ax1, -1, X, H, H, B * n0, n1 * H, s); }, reps, s);
-            if (t < best) best = t, pick = w;
+            if (t < best) best = t, pick = w, pick_tma = 0;
         }
         p->choice_w1 = pick;
+        p->choice_tma1 = pick_tma;
     }
     // n0 pass: the TMA kernel or the plain kernel at several widths
     if (p->ax0.L > 1 && p->ax0.spec && !p->ax0.tc) {

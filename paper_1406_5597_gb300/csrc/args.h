@@ -73,6 +73,7 @@ struct LenEntry {
     ColFn col_fwd, col_inv;
     int tma_E, tma_W;  // TMA-fed persistent column kernel (tma_W = 0: none)
     ColTmaFn tma_fwd, tma_inv;
+    ColTmaFn tma_pair_fwd, tma_pair_inv;  // same, for an odd axis stride (row-pair view)
     int row_E, row_rows;  // row kernels (row_E = 0: none)
     bool row_warp;        // rows resident in warps (shuffle unpack) or staged in shared memory
     RowFn r2c, c2r;

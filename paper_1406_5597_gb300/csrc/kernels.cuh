@@ -482,21 +482,31 @@ __global__ void __launch_bounds__(W*(L / E)) col_pipe_kernel(ColArgs a, long lon
 // from registers to global memory.  Every mbarrier wait is bounded: a wait
 // that gives up sets kStatusTimeout in the device status word, and the CTA
 // drains its outstanding copies (again bounded) before returning.
-// Requirements (checked by the host): 8*S and the base address 16-byte
-// aligned, Bs == L*S, W*8 a multiple of 16.
+// Requirements (checked by the host): the base address 16-byte aligned,
+// Bs == L*S, W*8 a multiple of 16, and 8*S a multiple of 16.
+//
+// PAIR mode lifts the last one (an odd axis stride S, e.g. the n1 pass with
+// H = n2/2+1 odd): the volume is viewed as PAIRS of rows (stride 16*S bytes,
+// inner extent 2*S complex), the even rows of a tile come as a box starting
+// at column c0, the odd rows as a box starting at column c0-1 of the second
+// row of the pair (H + c0 - 1 is even, so the start stays 16-byte aligned);
+// both boxes are W+2 columns wide and the reads index past the offset.
 // ---------------------------------------------------------------------------
 constexpr unsigned kMbarMaxTries = 1u << 20;
 
-template <int L, int E, int DIR, int W, int STAGES, int PF = 0>
+template <int L, int E, int DIR, int W, int STAGES, int PF = 0, bool PAIR = false>
 __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constant__ CUtensorMap tmap, ColArgs a,
                                                            long long ntiles)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
     constexpr int T = L / E;
-    constexpr int BOXR = L < 256 ? L : 256;
-    constexpr int NBOX = L / BOXR;
-    static_assert(L % BOXR == 0, "tile rows must split into boxes of <= 256 rows");
-    constexpr unsigned TILE_BYTES = (unsigned)L * W * sizeof(float2);
+    constexpr int ROWS_IN_MAP = PAIR ? L / 2 : L;  // tensor rows per tile (row pairs in PAIR mode)
+    constexpr int BOXR = ROWS_IN_MAP < 256 ? ROWS_IN_MAP : 256;
+    constexpr int NBOX = ROWS_IN_MAP / BOXR;
+    static_assert(ROWS_IN_MAP % BOXR == 0, "tile rows must split into boxes of <= 256 rows");
+    static_assert(!PAIR || (L % 2 == 0 && W % 2 == 0), "row pairs need even L and W");
+    constexpr int WS = PAIR ? W + 2 : W;  // slot row width (complex values)
+    constexpr unsigned TILE_BYTES = (unsigned)L * WS * sizeof(float2);
     float2* ring = reinterpret_cast<float2*>(smraw);
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(smraw + (size_t)STAGES * TILE_BYTES);
     const int c = threadIdx.x;
@@ -518,19 +528,30 @@ __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constan
     auto issue = [&](long long tile, int s) {
         if (tile >= ntiles) return;
         const long long b = tile / ctiles;
-        const int x = (int)(2 * (tile - b * ctiles) * W);
+        const long long c0 = (tile - b * ctiles) * W;
+        const int x = (int)(2 * c0);
         mbar_arrive_expect_tx(&bars[s], TILE_BYTES);
+        float2* slot = ring + (size_t)s * L * WS;
 #pragma unroll
-        for (int k = 0; k < NBOX; ++k)
-            tma_load_2d(ring + (size_t)s * L * W + (size_t)k * BOXR * W, &tmap, x, (int)(b * L + k * BOXR), &bars[s]);
+        for (int k = 0; k < NBOX; ++k) {
+            const int y = (int)(b * ROWS_IN_MAP + k * BOXR);
+            tma_load_2d(slot + (size_t)k * BOXR * WS, &tmap, x, y, &bars[s]);
+            if constexpr (PAIR)
+                tma_load_2d(slot + (size_t)(L / 2) * WS + (size_t)k * BOXR * WS, &tmap, (int)(2 * (a.S + c0 - 1)), y,
+                            &bars[s]);
+        }
         ++uses[s];
         if constexpr (PF > 0) {  // warm L2 with the tile PF ring-lengths further on
             const long long pt = tile + (long long)PF * gridDim.x;
             if (pt < ntiles) {
                 const long long pb = pt / ctiles;
-                const int px = (int)(2 * (pt - pb * ctiles) * W);
+                const long long pc0 = (pt - pb * ctiles) * W;
 #pragma unroll
-                for (int k = 0; k < NBOX; ++k) tma_prefetch_l2_2d(&tmap, px, (int)(pb * L + k * BOXR));
+                for (int k = 0; k < NBOX; ++k) {
+                    const int y = (int)(pb * ROWS_IN_MAP + k * BOXR);
+                    tma_prefetch_l2_2d(&tmap, (int)(2 * pc0), y);
+                    if constexpr (PAIR) tma_prefetch_l2_2d(&tmap, (int)(2 * (a.S + pc0 - 1)), y);
+                }
             }
         }
     };
@@ -557,10 +578,18 @@ __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constan
         const long long b = tile / ctiles;
         const long long c0 = (tile - b * ctiles) * W;
         const bool active = (c0 + c) < a.C;
-        float2* buf = ring + (size_t)stage * L * W;
+        float2* buf = ring + (size_t)stage * L * WS;
         float2 v[E];
+        if constexpr (PAIR) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = buf[(t + T * m) * W + c];
+            for (int m = 0; m < E; ++m) {
+                const int j = t + T * m;  // even rows: box from c0; odd rows: box from c0 - 1
+                v[m] = (j & 1) ? buf[(L / 2) * WS + (j >> 1) * WS + c + 1] : buf[(j >> 1) * WS + c];
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = buf[(t + T * m) * W + c];
+        }
         __syncthreads();  // the slot now serves as the exchange buffer
         ColExchange exch{buf, W, c};
         fft_group<L, E, DIR>(v, t, a.tw, exch);
@@ -701,12 +730,13 @@ inline cudaError_t launch_col_pipe(const ColArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int L, int E, int W, int STAGES, int DIR, int PF = 0>
+template <int L, int E, int W, int STAGES, int DIR, int PF = 0, bool PAIR = false>
 inline cudaError_t launch_col_tma(const ColArgs& a, const CUtensorMap& map, cudaStream_t s)
 {
     constexpr int T = L / E;
-    const size_t smem = (size_t)STAGES * L * W * sizeof(float2) + STAGES * sizeof(unsigned long long);
-    auto k = col_tma_kernel<L, E, DIR, W, STAGES, PF>;
+    constexpr int WS = PAIR ? W + 2 : W;
+    const size_t smem = (size_t)STAGES * L * WS * sizeof(float2) + STAGES * sizeof(unsigned long long);
+    auto k = col_tma_kernel<L, E, DIR, W, STAGES, PF, PAIR>;
     static int per_sm = 0;
     static int sms = 0;
     if (per_sm == 0) {
@@ -727,9 +757,9 @@ inline cudaError_t launch_col_tma(const ColArgs& a, const CUtensorMap& map, cuda
     return cudaGetLastError();
 }
 
-inline cudaError_t col_tensor_map(CUtensorMap* map, const ColArgs& a, int L, int W)
+inline cudaError_t col_tensor_map(CUtensorMap* map, const ColArgs& a, int L, int W, bool pair = false)
 {
-    return col_tensor_map_host(map, a, L, W);
+    return col_tensor_map_host(map, a, L, W, pair);
 }
 
 }  // namespace fft3d

@@ -28,10 +28,14 @@ cudaError_t encode_tensor_map_2d(CUtensorMap* map, const void* base, unsigned lo
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t col_tensor_map_host(CUtensorMap* map, const ColArgs& a, int L, int W)
+cudaError_t col_tensor_map_host(CUtensorMap* map, const ColArgs& a, int L, int W, bool pair)
 {
-    return encode_tensor_map_2d(map, a.data, 2ull * a.C, (unsigned long long)a.nb * L, 8ull * a.S, 2u * W,
-                                L < 256 ? L : 256);
+    if (!pair)
+        return encode_tensor_map_2d(map, a.data, 2ull * a.C, (unsigned long long)a.nb * L, 8ull * a.S, 2u * W,
+                                    L < 256 ? L : 256);
+    const int rows = L / 2;
+    return encode_tensor_map_2d(map, a.data, 4ull * a.S, (unsigned long long)a.nb * rows, 16ull * a.S,
+                                2u * (W + 2), rows < 256 ? rows : 256);
 }
 
 }  // namespace fft3d

@@ -13,7 +13,9 @@ cudaError_t encode_tensor_map_2d(CUtensorMap* map, const void* base, unsigned lo
 
 struct ColArgs;
 // Tensor map of a column pass for the TMA column kernel: 2D FP32 view, inner
-// 2*C floats, outer nb*L rows of byte stride 8*S, box (2*W floats) x min(L, 256).
-cudaError_t col_tensor_map_host(CUtensorMap* map, const ColArgs& a, int L, int W);
+// 2*C floats, outer nb*L rows of byte stride 8*S, box (2*W floats) x min(L, 256);
+// pair mode: inner 4*S floats (a row pair), outer nb*L/2 pairs of byte
+// stride 16*S, box (2*(W+2) floats) x min(L/2, 256).
+cudaError_t col_tensor_map_host(CUtensorMap* map, const ColArgs& a, int L, int W, bool pair = false);
 
 }  // namespace fft3d

@@ -1,8 +1,8 @@
 """Autotuning cache ("wisdom"): kernel shape choices per GPU and transform.
 
 fft3d_autotune (C) times the candidate shapes of every pass on the caller's
-buffers and keeps the fastest; this module stores the chosen four integers
-{w0, w1, rows, tma} in a JSON file so later plans of the same GPU model and
+buffers and keeps the fastest; this module stores the chosen five integers
+{w0, w1, rows, tma0, tma1} in a JSON file so later plans of the same GPU model and
 shape reuse them without tuning.  File: $FFT3D_TUNE_CACHE, else
 ~/.cache/fft3d_wisdom.json.
 """
@@ -56,7 +56,7 @@ def tuned_plan(n0, n1, n2, batch=1, dtype=FFT3D_F32, flags=0, reps=5, path=None,
     gpu = torch.cuda.get_device_name()
     key = cache_key(gpu, (n0, n1, n2), batch, dtype, flags)
     cached = None if retune else load_cache(path).get(key)
-    if cached is not None:
+    if cached is not None and len(cached) == 5:
         st = fft3d_set_choices(plan.handle, cached)
         if st != FFT3D_OK:
             raise Fft3dError(st, "fft3d_set_choices")

@@ -125,6 +125,8 @@ SHAPES = [
     (512, 6, 10), (512, 5, 6), (256, 3, 4), (256, 40, 60), (1024, 6, 12),
     # warp-resident rows at n2 = 1024, shared-memory rows at n2 = 2048
     (8, 6, 1024), (3, 2, 2048),
+    # n1 pass through the TMA kernel: row pairs (odd H) with ragged tiles, plain rows (even H)
+    (6, 512, 60), (3, 256, 40), (4, 1024, 30), (5, 256, 512),
 ]
 
 
@@ -435,14 +437,14 @@ def test_autotune_keeps_parity_and_choices_roundtrip(cuda_lib):
     cplx = torch.empty(n0 * n1 * (n2 // 2 + 1), dtype=torch.complex64, device="cuda")
     assert lib.fft3d_autotune(plan.handle, real.data_ptr(), cplx.data_ptr(), 2) == lib.FFT3D_OK
     ch = lib.fft3d_get_choices(plan.handle)
-    assert len(ch) == 4 and ch[3] in (0, 1)
+    assert len(ch) == 5 and ch[3] in (0, 1) and ch[4] in (0, 1)
     x32 = synth.uniform_field((n0, n1, n2), seed=91).astype(np.float32)
     xd = torch.from_numpy(x32).cuda()
     X = torch.empty((n0, n1, n2 // 2 + 1), dtype=torch.complex64, device="cuda")
     plan.r2c(xd.data_ptr(), X.data_ptr())
     assert rel_l2(X.cpu().numpy(), oracle.r2c3d(x32.astype(np.float64))) <= TOL
     # every candidate shape gives the same transform
-    for choice in ([0, 0, 0, 1], [4, 8, 2, 0], [8, 16, 4, 0]):
+    for choice in ([0, 0, 0, 1, 1], [4, 8, 2, 0, 0], [8, 16, 4, 0, 1], [0, 0, 0, 1, 0]):
         assert lib.fft3d_set_choices(plan.handle, choice) == lib.FFT3D_OK
         assert lib.fft3d_get_choices(plan.handle) == choice
         plan.r2c(xd.data_ptr(), X.data_ptr())
@@ -451,7 +453,7 @@ def test_autotune_keeps_parity_and_choices_roundtrip(cuda_lib):
         y = torch.empty_like(xd)
         plan.c2r(Y.data_ptr(), y.data_ptr())
         assert rel_l2(y.cpu().numpy() / (n0 * n1 * n2), x32.astype(np.float64)) <= TOL_RT
-    assert lib.fft3d_set_choices(plan.handle, [0, 0, 0, 2]) == lib.FFT3D_ERR_INVALID_ARG
+    assert lib.fft3d_set_choices(plan.handle, [0, 0, 0, 2, 0]) == lib.FFT3D_ERR_INVALID_ARG
 
 
 def test_tuned_plan_uses_the_cache(cuda_lib, tmp_path):

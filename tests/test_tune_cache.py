@@ -10,10 +10,10 @@ def test_cache_roundtrip_and_merge(tmp_path):
     k1 = tune.cache_key("NVIDIA GB300", (512, 512, 512), 1, 0, 0)
     k2 = tune.cache_key("NVIDIA GB300", (64, 64, 64), 4, 0, 0)
     assert k1 != k2 and "512x512x512" in k1
-    tune.store_cache({k1: [8, 4, 2, 1]}, p)
-    tune.store_cache({k2: [0, 16, 4, 0]}, p)
+    tune.store_cache({k1: [8, 4, 2, 1, 1]}, p)
+    tune.store_cache({k2: [0, 16, 4, 0, 1]}, p)
     data = tune.load_cache(p)
-    assert data[k1] == [8, 4, 2, 1] and data[k2] == [0, 16, 4, 0]
+    assert data[k1] == [8, 4, 2, 1, 1] and data[k2] == [0, 16, 4, 0, 1]
     json.loads(open(p).read())
 
 
