@@ -45,10 +45,13 @@ def dist_env():
 
 
 def workload_config(n, args):
+    n0, n1, n2 = args.shape
+    field = ("spectrum-shaped velocity component (seed 1408)" if args.field == "spectrum"
+             else "seeded uniform[-1,1) field (torch generator, seed 1408)")
     return {
-        "workload": f"{n}x{n}x{n} FP32 r2c+c2r, transpose-free, spectrum-shaped velocity component (seed 1408)",
-        "n0": n, "n1": n, "n2": n, "batch": 1,
-        "bytes_per_step": two_pass_bytes(n, n, n)[0],
+        "workload": f"{n0}x{n1}x{n2} FP32 r2c+c2r, transpose-free, {field}",
+        "n0": n0, "n1": n1, "n2": n2, "batch": 1,
+        "bytes_per_step": two_pass_bytes(n0, n1, n2)[0],
         "bytes_definition": "2*(4N+24M): one read + one write per pass of the 2-pass minimum, r2c and c2r",
         "l2": "inputs larger than L2 (0.54 GB real + 0.54 GB complex per field), no flush",
         "parallelism": f"replicas x{args.gpus}",
@@ -144,10 +147,14 @@ class ClockSampler:
 
 def make_field(n):
     """Spectrum-shaped half spectrum S (complex64 numpy) of velocity component 0."""
+    return make_field_shape(n, n, n)
+
+
+def make_field_shape(n0, n1, n2):
     import numpy as np
 
     import synth
-    S = synth.spectral_velocity(n, n, n, seed=synth.seed_for_config(2), components=(0,))[0]
+    S = synth.spectral_velocity(n0, n1, n2, seed=synth.seed_for_config(2), components=(0,))[0]
     return S.astype(np.complex64)
 
 
@@ -207,13 +214,19 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fft3d", choices=["fft3d", "reference"])
-    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--n", type=int, default=512, help="cubic size (default workload 512^3)")
+    ap.add_argument("--shape", type=str, default=None, help="n0,n1,n2 (overrides --n)")
+    ap.add_argument("--field", default="spectrum", choices=["spectrum", "uniform"],
+                    help="input field; uniform skips the host-side spectrum generator (large sizes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--tc", action="store_true", help="time the tensor-core forms even with --no-variants")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the compiled kernel shapes")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    args.shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else (args.n, args.n, args.n)
 
     if args.impl == "reference":
         run_reference(args)
@@ -232,18 +245,30 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     fft3d.load()
     n = args.n
-    nbytes, N, M = two_pass_bytes(n, n, n)
+    n0, n1, n2 = args.shape
+    nbytes, N, M = two_pass_bytes(n0, n1, n2)
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
 
-    plan = fft3d.Plan(n, n, n)
-    S = make_field(n)
-    Sd = torch.from_numpy(S).to(dev)
-    x = torch.empty((n, n, n), dtype=torch.float32, device=dev)
-    plan.c2r(Sd.data_ptr(), x.data_ptr(), sptr)  # the real field (setup)
-    del Sd
-    X = torch.empty((n, n, n // 2 + 1), dtype=torch.complex64, device=dev)
+    plan = fft3d.Plan(n0, n1, n2)
+    x = torch.empty((n0, n1, n2), dtype=torch.float32, device=dev)
+    S = None
+    if args.field == "spectrum":
+        S = make_field_shape(n0, n1, n2)
+        Sd = torch.from_numpy(S).to(dev)
+        plan.c2r(Sd.data_ptr(), x.data_ptr(), sptr)  # the real field (setup)
+        del Sd
+    else:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(1408)
+        x.uniform_(-1.0, 1.0, generator=gen)
+    X = torch.empty((n0, n1, n2 // 2 + 1), dtype=torch.complex64, device=dev)
     y = torch.empty_like(x)
+    if not args.no_autotune:  # the library's autotuner picks the kernel shapes (untimed set-up)
+        yf = y.view(-1)
+        st = fft3d.fft3d_autotune(plan.handle, yf.data_ptr(), X.data_ptr(), 3, sptr)
+        if st != fft3d.FFT3D_OK:
+            raise fft3d.Fft3dError(st, "fft3d_autotune")
 
     def step():
         plan.r2c(x.data_ptr(), X.data_ptr(), sptr)
@@ -293,7 +318,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(n, args),
         "frac_of_8tbs": value / world / 8000.0, "frac_of_measured_copy": value / world / peak,
         "roofline": roofline, "passes": passes, "gpu_launches": launches, "clocks": clocks,
-        "plan": plan.describe(),
+        "plan": plan.describe(), "choices": fft3d.fft3d_get_choices(plan.handle),
+        "autotuned": not args.no_autotune,
     }
 
     # comparator: the explicit-transpose variant (+1 pass), and with transpose-back (+2)
@@ -303,7 +329,7 @@ def main():
                             ("explicit_transpose_back", fft3d.FFT3D_FLAG_EXPLICIT_TRANSPOSE
                              | fft3d.FFT3D_FLAG_TRANSPOSE_BACK),
                             ("fused_plane", fft3d.FFT3D_FLAG_FUSED_PLANE)):
-            vp = fft3d.Plan(n, n, n, flags=flags)
+            vp = fft3d.Plan(n0, n1, n2, flags=flags)
 
             def vstep(vp=vp):
                 vp.r2c(x.data_ptr(), X.data_ptr(), sptr)
@@ -318,19 +344,31 @@ def main():
         line["variants"] = variants
 
     # tensor-core radix-16 forms (split-BF16 x3, FP16) of the same step, with
-    # their accuracy against the exact spectrum N*S of the field (x = c2r(S))
-    if not args.no_variants:
-        Sd = torch.from_numpy(S).to(dev)
-        Nn = float(n) ** 3
+    # their accuracy against the exact spectrum N*S of the field (x = c2r(S)),
+    # or (uniform field) against the FP32 path's spectrum
+    if not args.no_variants or args.tc:
+        Nn = float(n0 * n1 * n2)
+        if S is not None:
+            Sref = Nn * torch.from_numpy(S).to(dev)  # complex64 copy; differences in FP64 per chunk
+        else:
+            plan.r2c(x.data_ptr(), X.data_ptr(), sptr)
+            Sref = X.clone()
 
         def rel_vs_exact(Xc):
-            d = Xc.to(torch.complex128) - Nn * Sd.to(torch.complex128)
-            return float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(Nn * Sd.to(torch.complex128)))
+            num = 0.0
+            den = 0.0
+            step = max(1, (1 << 26) // (n1 * (n2 // 2 + 1)))  # about 512 MB of complex128 per chunk
+            for a0 in range(0, n0, step):
+                r = Sref[a0:a0 + step].to(torch.complex128)
+                d = Xc[a0:a0 + step].to(torch.complex128) - r
+                num += float(torch.sum(d.real ** 2 + d.imag ** 2))
+                den += float(torch.sum(r.real ** 2 + r.imag ** 2))
+            return (num / den) ** 0.5
 
         plan.r2c(x.data_ptr(), X.data_ptr(), sptr)
         tc = {"fp32": {"ms_per_step": ms, "rel_l2_r2c_vs_exact": rel_vs_exact(X)}}
         for name, dt in (("tc_bf16x3", fft3d.FFT3D_F32_TC_BF16X3), ("tc_f16", fft3d.FFT3D_F32_TC_F16)):
-            tp = fft3d.Plan(n, n, n, dtype=dt)
+            tp = fft3d.Plan(n0, n1, n2, dtype=dt)
             tp.r2c(x.data_ptr(), X.data_ptr(), sptr)
             err = rel_vs_exact(X)
 
@@ -344,8 +382,9 @@ def main():
             tc[name] = {"ms_per_step": tms, "gbs_effective": nbytes / (tms * 1e-3) / 1e9,
                         "rel_l2_r2c_vs_exact": err, "speed_vs_fp32": ms / tms, "plan": tp.describe()}
             tp.close()
+        tc["reference"] = "exact spectrum N*S" if S is not None else "FP32 path spectrum"
         line["tensor_core_forms"] = tc
-        del Sd
+        del Sref
 
     # pseudo-spectral nonlinear term at 256^3 (3 velocity spectra in, 6 dealiased
     # product spectra out), replayed as one CUDA graph
@@ -432,11 +471,11 @@ def main():
         xs = x.cpu().numpy().astype(np.float64)
         t0 = time.perf_counter()
         Xo = oracle.r2c3d(xs)
-        oracle.c2r3d(Xo, n)
+        oracle.c2r3d(Xo, n2)
         t_cpu = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": nbytes / t_cpu / 1e9, "unit": UNIT, "cores": oracle.threads(),
                                 "kind": "oracle", "ms_per_step": 1e3 * t_cpu,
-                                "sample": f"one full {n}^3 r2c+c2r of the same field in FP64"}
+                                "sample": f"one full {n0}x{n1}x{n2} r2c+c2r of the same field in FP64"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

@@ -12,10 +12,14 @@
 #define FFT3D_TMA(L, E, W, ST, PF, PST)                                                                   \
     E, W, &fft3d::launch_col_tma<L, E, W, ST, -1, PF>, &fft3d::launch_col_tma<L, E, W, ST, 1, PF>,        \
         &fft3d::launch_col_tma<L, E, W, PST, -1, PF, true>, &fft3d::launch_col_tma<L, E, W, PST, 1, PF, true>
+#define FFT3D_TMA_NOPAIR(L, E, W, ST, PF) \
+    E, W, &fft3d::launch_col_tma<L, E, W, ST, -1, PF>, &fft3d::launch_col_tma<L, E, W, ST, 1, PF>, nullptr, nullptr
 // warp-resident rows (T = L/E <= 32), ROWS rows per CTA
 #define FFT3D_ROWW(L, E, R)                                                                              \
     E, R, true, &fft3d::launch_row_warp<L, E, R, -1>, &fft3d::launch_row_warp<L, E, R, 1>,              \
         &fft3d::launch_row_nonlinear<L, E, R>
+// warp-resident rows without the fused nonlinear-term kernel (too many registers at this length)
+#define FFT3D_ROWW_NONL(L, E, R) E, R, true, &fft3d::launch_row_warp<L, E, R, -1>, &fft3d::launch_row_warp<L, E, R, 1>, nullptr
 // shared-memory staged rows
 #define FFT3D_ROWS(L, E, R) E, R, false, &fft3d::launch_row<L, E, R, -1>, &fft3d::launch_row<L, E, R, 1>, nullptr
 #define FFT3D_NO_ROW 0, 0, false, nullptr, nullptr, nullptr

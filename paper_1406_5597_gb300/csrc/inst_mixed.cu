@@ -10,7 +10,7 @@ const LenEntry* entries_mixed(int* n)
         {96, FFT3D_COL(96, 24, 64), FFT3D_NO_TMA, FFT3D_ROWW(96, 24, 16)},
         {160, FFT3D_COL(160, 20, 32), FFT3D_NO_TMA, FFT3D_NO_ROW},
         {192, FFT3D_COL(192, 24, 32), FFT3D_NO_TMA, FFT3D_NO_ROW},
-        {1536, FFT3D_COL(1536, 24, 8), FFT3D_NO_TMA, FFT3D_NO_ROW},
+        {1536, FFT3D_COL(1536, 24, 8), FFT3D_TMA_NOPAIR(1536, 24, 8, 2, 0), FFT3D_NO_ROW},
     };
     *n = (int)(sizeof(e) / sizeof(e[0]));
     return e;

@@ -136,7 +136,8 @@ __device__ __forceinline__ void twiddle_inputs(float2* a, const float2* __restri
     }
 }
 
-template <int L, int E, int DIR, int S>
+// TS: the twiddle table has length L*TS (W_L^x = table[x*TS]).
+template <int L, int E, int DIR, int S, int TS = 1>
 struct Stage {
     template <class Ex>
     __device__ __forceinline__ static void run(float2 (&v)[E], int t, const float2* __restrict__ tw, const Ex& ex)
@@ -157,7 +158,7 @@ struct Stage {
             const int jm = j % Ns;
             if constexpr (Ns > 1) {
                 constexpr int step = L / (Ns * R);
-                twiddle_inputs<R, DIR>(a, tw, jm * step);
+                twiddle_inputs<R, DIR>(a, tw, jm * step * TS);
             }
             Dft<R, DIR>::run(a);
             if constexpr (last) {
@@ -174,17 +175,18 @@ struct Stage {
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = ex.get(t + T * m);
             ex.sync();
-            Stage<L, E, DIR, S + 1>::run(v, t, tw, ex);
+            Stage<L, E, DIR, S + 1, TS>::run(v, t, tw, ex);
         }
     }
 };
 
 // Full transform: v holds positions t + T*m on entry and their DFT on exit.
-template <int L, int E, int DIR, class Ex>
+// TS > 1: the twiddle table belongs to a TS times longer transform.
+template <int L, int E, int DIR, int TS = 1, class Ex>
 __device__ __forceinline__ void fft_group(float2 (&v)[E], int t, const float2* __restrict__ tw, const Ex& ex)
 {
     static_assert(num_stages(L, E) > 0, "L must factor into radices dividing E");
-    Stage<L, E, DIR, 0>::run(v, t, tw, ex);
+    Stage<L, E, DIR, 0, TS>::run(v, t, tw, ex);
 }
 
 }  // namespace fft3d

@@ -126,7 +126,7 @@ SHAPES = [
     # warp-resident rows at n2 = 1024, shared-memory rows at n2 = 2048
     (8, 6, 1024), (3, 2, 2048),
     # n1 pass through the TMA kernel: row pairs (odd H) with ragged tiles, plain rows (even H)
-    (6, 512, 60), (3, 256, 40), (4, 1024, 30), (5, 256, 512),
+    (6, 512, 60), (3, 256, 40), (4, 1024, 30), (5, 256, 512), (1536, 4, 12),
 ]
 
 
