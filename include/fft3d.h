@@ -78,6 +78,10 @@ typedef enum {
                                              kernel that keeps each plane in L2 between its halves
                                              (DRAM traffic of two passes; shapes with an instantiated
                                              fused kernel only, else ignored) */
+#define FFT3D_FLAG_CLUSTER_PLANE 0x40     /* fuse the n2-row and n1-column passes into one kernel that holds
+                                             each plane in the distributed shared memory of a thread-block
+                                             cluster (DRAM traffic of two passes; shapes with an
+                                             instantiated cluster kernel only, else ignored) */
 #define FFT3D_FLAG_TEST_SKIP_ARRIVAL 0x10 /* testing only (with FUSED_PLANE): in the fused plane kernel the producers of
                                              plane 0 never report, so its consumers' bounded waits give
                                              up after about a millisecond; the call's output is then

@@ -39,6 +39,7 @@ FFT3D_FLAG_THREE_PASS = 0x4
 FFT3D_FLAG_GENERIC = 0x8
 FFT3D_FLAG_TEST_SKIP_ARRIVAL = 0x10
 FFT3D_FLAG_FUSED_PLANE = 0x20
+FFT3D_FLAG_CLUSTER_PLANE = 0x40
 
 _lib = None
 _lock = threading.Lock()

@@ -23,6 +23,7 @@
 #include "args.h"
 #include "energy.h"
 #include "fft3d.h"
+#include "cplane.h"
 #include "plane.h"
 #include "tma_host.h"
 
@@ -196,6 +197,7 @@ struct fft3d_plan_s {
     float2* d_twpack = nullptr;
     int* d_status = nullptr;
     const PlaneEntry* plane = nullptr;  // fused n2+n1 kernel, when one fits this shape
+    const CPlaneEntry* cplane = nullptr;  // cluster (distributed shared memory) n2+n1 kernel
     uint16_t* d_tcg = nullptr;          // tensor-core DFT operand table (TC dtypes)
     int* d_counters = nullptr;          // per-plane completion counters + work ticket of the fused kernel
     float2* d_ring = nullptr;           // inverse fused kernel: L2-resident ring of n1-transformed planes
@@ -413,6 +415,21 @@ cudaError_t run_plane(fft3d_plan_s* p, int dir, const void* in, void* out, cudaS
     return dir < 0 ? p->plane->fwd(a, s) : p->plane->inv(a, s);
 }
 
+// The cluster plane pass (rows + n1 columns of every plane, one cluster per plane).
+cudaError_t run_cplane(fft3d_plan_s* p, int dir, const void* in, void* out, cudaStream_t s)
+{
+    ProfScope ps(p, dir < 0 ? PASS_PLANE_FWD : PASS_PLANE_INV, s);
+    CPlaneArgs a;
+    a.in = in;
+    a.out = out;
+    a.planes = (long long)p->batch * p->n0;
+    a.tw_row = p->ax2.d_tw;
+    a.twpack = p->d_twpack;
+    a.tw_col = p->ax1.d_tw;
+    a.status = p->d_status;
+    return dir < 0 ? p->cplane->fwd(a, s) : p->cplane->inv(a, s);
+}
+
 cudaError_t run_swap(fft3d_plan_s* p, const float2* in, float2* out, long long a0, long long a1, cudaStream_t s)
 {
     ProfScope ps(p, PASS_SWAP01, s);
@@ -424,6 +441,12 @@ std::string describe_plan(const fft3d_plan_s* p)
     const int flags = p->flags;
     std::string d = "rows[" + axis_desc(p, p->ax2, true) + "] n1[" + axis_desc(p, p->ax1, false) + "] n0[" +
                     axis_desc(p, p->ax0, false) + "]";
+    if (p->cplane) {
+        char b[128];
+        std::snprintf(b, sizeof b, "cluster-plane[%d CTAs x %d rows, %d threads]", p->cplane->C,
+                      p->cplane->LC / p->cplane->C, p->cplane->NT);
+        d = std::string(b) + " n0[" + axis_desc(p, p->ax0, false) + "]";
+    }
     if (p->plane) {
         char b[128];
         std::snprintf(b, sizeof b, "plane[fused rows E=%d + n1 E=%d, %d threads]", p->plane->ER, p->plane->EC,
@@ -466,7 +489,8 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
 {
     if (n0 < 1 || n1 < 1 || n2 < 2 || batch < 1 || dtype < 0 || dtype > 2 ||
         (flags & ~(FFT3D_FLAG_EXPLICIT_TRANSPOSE | FFT3D_FLAG_TRANSPOSE_BACK | FFT3D_FLAG_THREE_PASS |
-                   FFT3D_FLAG_GENERIC | FFT3D_FLAG_TEST_SKIP_ARRIVAL | FFT3D_FLAG_FUSED_PLANE)) ||
+                   FFT3D_FLAG_GENERIC | FFT3D_FLAG_TEST_SKIP_ARRIVAL | FFT3D_FLAG_FUSED_PLANE |
+                   FFT3D_FLAG_CLUSTER_PLANE)) ||
         ((flags & FFT3D_FLAG_TRANSPOSE_BACK) && !(flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE))) {
         fail(FFT3D_ERR_INVALID_ARG);
         return nullptr;
@@ -476,7 +500,8 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
         fail(FFT3D_ERR_UNSUPPORTED_SIZE);
         return nullptr;
     }
-    if (dtype != FFT3D_F32 && (flags & (FFT3D_FLAG_EXPLICIT_TRANSPOSE | FFT3D_FLAG_GENERIC | FFT3D_FLAG_FUSED_PLANE))) {
+    if (dtype != FFT3D_F32 && (flags & (FFT3D_FLAG_EXPLICIT_TRANSPOSE | FFT3D_FLAG_GENERIC | FFT3D_FLAG_FUSED_PLANE |
+                                        FFT3D_FLAG_CLUSTER_PLANE))) {
         fail(FFT3D_ERR_INVALID_ARG);  // the tensor-core forms use the plain transpose-free pass sequence
         return nullptr;
     }
@@ -567,6 +592,13 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
             }
         }
     }
+    if ((flags & FFT3D_FLAG_CLUSTER_PLANE) && !p->plane &&
+        !(flags & (FFT3D_FLAG_THREE_PASS | FFT3D_FLAG_GENERIC | FFT3D_FLAG_EXPLICIT_TRANSPOSE))) {
+        int nc = 0;
+        const CPlaneEntry* ce = cplane_entries(&nc);
+        for (int i = 0; i < nc; ++i)
+            if (ce[i].LR == n2 / 2 && ce[i].LC == n1) p->cplane = &ce[i];
+    }
     {
         // energy scratch for nbins up to the largest shell of the shape
         const double kmax = std::sqrt((double)(n0 / 2) * (n0 / 2) + (double)(n1 / 2) * (n1 / 2) +
@@ -621,7 +653,7 @@ int fft3d_launches_per_call(fft3d_handle p, int dir)
 {
     if (!p) return fail(FFT3D_ERR_INVALID_ARG);
     (void)dir;
-    if (p->plane) return 1 + (p->n0 > 1);
+    if (p->plane || p->cplane) return 1 + (p->n0 > 1);
     int n = 1 + (p->n1 > 1) + (p->n0 > 1);
     if (p->flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE) n += (p->flags & FFT3D_FLAG_TRANSPOSE_BACK) ? 2 : 1;
     return n;
@@ -652,6 +684,11 @@ int fft3d_r2c(fft3d_handle p, const float* in, void* out, void* stream)
     const long long H = p->H, n0 = p->n0, n1 = p->n1, B = p->batch;
     float2* o = (float2*)out;
     cudaError_t e;
+    if (!xpose && p->cplane) {
+        if (run_cplane(p, -1, in, o, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_col(p, p->ax0, -1, o, p->P, p->P, B, p->M, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        return FFT3D_OK;
+    }
     if (!xpose && p->plane) {
         if (run_plane(p, -1, in, o, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
         if (run_col(p, p->ax0, -1, o, p->P, p->P, B, p->M, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
@@ -693,6 +730,11 @@ int fft3d_c2r(fft3d_handle p, void* in, float* out, void* stream)
     cudaStream_t s = (cudaStream_t)stream;
     const long long H = p->H, n0 = p->n0, n1 = p->n1, B = p->batch;
     float2* x = (float2*)in;
+    if (!xpose && p->cplane) {
+        if (run_col(p, p->ax0, +1, x, p->P, p->P, B, p->M, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        if (run_cplane(p, +1, x, out, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        return FFT3D_OK;
+    }
     if (!xpose && p->plane) {
         if (run_col(p, p->ax0, +1, x, p->P, p->P, B, p->M, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
         if (run_plane(p, +1, x, out, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);

@@ -1,0 +1,22 @@
+// Cluster plane kernels (n2 rows + n1 columns of a plane in one cluster's
+// distributed shared memory) for the (n2/2, n1) pairs of the cubic grids.
+#include "cplane.cuh"
+
+namespace fft3d {
+
+#define FFT3D_CPLANE(LR, ER, LC, C, NT, MINB) \
+    {LR, LC, C, NT, &launch_cplane<LR, ER, LC, C, NT, -1, MINB>, &launch_cplane<LR, ER, LC, C, NT, 1, MINB>}
+
+const CPlaneEntry* cplane_entries(int* n)
+{
+    static const CPlaneEntry e[] = {
+        FFT3D_CPLANE(16, 8, 32, 2, 32, 1),      // 32^3: 2 CTAs x 16 rows
+        FFT3D_CPLANE(64, 8, 128, 2, 256, 2),    // 128^3: 2 CTAs x 64 rows
+        FFT3D_CPLANE(128, 8, 256, 4, 256, 2),   // 256^3: 4 CTAs x 64 rows
+        FFT3D_CPLANE(256, 16, 512, 8, 512, 1),  // 512^3: 8 CTAs x 64 rows
+    };
+    *n = (int)(sizeof(e) / sizeof(e[0]));
+    return e;
+}
+
+}  // namespace fft3d

@@ -180,10 +180,15 @@ __global__ void __launch_bounds__((L / E) * ROWS) row_c2r_kernel(RowArgs a)
 // register (E-m) mod E.  One warp shuffle per value replaces a shared-memory
 // round trip.  The unpack twiddle W_{2L}^k is formed as W_{2L}^t * W_{2L}^{T m}.
 // ---------------------------------------------------------------------------
-template <bool CG>
+// Load policy of the row / column bodies: 0 read-only path (__ldg), 1 L2 only
+// (__ldcg: data another CTA wrote during this launch), 2 plain load (shared
+// memory, through a generic pointer).
+constexpr int kLdNc = 0, kLdCg = 1, kLdPlain = 2;
+template <int CG>
 __device__ __forceinline__ float2 ld2(const float2* p)
 {
-    if constexpr (CG) return __ldcg(p);  // L2 only: data another CTA wrote during this launch
+    if constexpr (CG == kLdCg) return __ldcg(p);
+    else if constexpr (CG == kLdPlain) return *p;
     else return __ldg(p);
 }
 
@@ -193,14 +198,15 @@ __device__ __forceinline__ float2 ld2(const float2* p)
 // all; the 2/3 rule keeps 3*k2 < n2).  t in [0, T); lane = the thread's lane;
 // the T threads of a row are consecutive lanes.  sm_row: RowLayout<L>::stride
 // float2 of exchange space.
-template <int L, int E>
+// Ex: the exchange policy over sm_row (the warp-synchronous padded row by default).
+template <int L, int E, class Ex = RowExchange<true>>
 __device__ __forceinline__ void row_r2c_regs(float2 (&v)[E], float2* out_row, bool active, int t, int lane,
                                              float2* sm_row, const float2* __restrict__ tw,
                                              const float2* __restrict__ twpack, int k2_keep = L + 1)
 {
     constexpr int T = L / E;
     static_assert(T <= 32 && (32 % T) == 0, "rows must pack into warps");
-    RowExchange<true> ex{sm_row};
+    Ex ex{sm_row};
     fft_group<L, E, -1>(v, t, tw, ex);
     const int partner = lane - t + ((T - t) & (T - 1));
     const float2 wt = __ldg(&twpack[t]);
@@ -237,7 +243,9 @@ __device__ __forceinline__ void row_r2c_body(const float2* in_row, float2* out_r
 
 // c2r of one row of H bins into registers: v[m] = the real samples 2p, 2p+1
 // at position p = t + T*m (unnormalised).
-template <int L, int E, bool CG>
+// Ex: the exchange policy over sm_row; sm_row may alias in_row (every lane's
+// reads of in_row complete before the first exchange write).
+template <int L, int E, int CG, class Ex = RowExchange<true>>
 __device__ __forceinline__ void row_c2r_regs(const float2* in_row, bool active, int t, int lane, float2* sm_row,
                                              const float2* __restrict__ tw, const float2* __restrict__ twpack,
                                              float2 (&v)[E])
@@ -273,7 +281,8 @@ __device__ __forceinline__ void row_c2r_regs(const float2* in_row, bool active, 
         const float2 wd = cmulc(d, w);  // Z = s + i W^{-k} d
         v[m] = make_float2(s.x - wd.y, s.y + wd.x);
     }
-    RowExchange<true> ex{sm_row};
+    Ex ex{sm_row};
+    ex.sync();
     fft_group<L, E, +1>(v, t, tw, ex);
 }
 

@@ -1,10 +1,11 @@
-// Register-resident small DFT codelets (radix 2, 3, 4, 5, 8, 16) in FP32.
+// Register-resident small DFT codelets (radix 2, 3, 4, 5, 8, 16, 32) in FP32.
 //
 // DIR = -1 is the forward kernel exp(-2 pi i / R), DIR = +1 the inverse.
 // Every codelet maps a[0..R-1] (natural order) to its DFT (natural order),
-// in place, unnormalised.  The composite radices 8 = 2 x 4 and 16 = 4 x 4 are
-// Cooley-Tukey splits with their inner twiddles as exact compile-time
-// constants (values of cos/sin at multiples of pi/8, written to 20 digits).
+// in place, unnormalised.  The composite radices 8 = 2 x 4, 16 = 4 x 4 and
+// 32 = 4 x 8 are Cooley-Tukey splits with their inner twiddles as exact
+// compile-time constants (values of cos/sin at multiples of pi/16, written to
+// 20 digits).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -38,33 +39,40 @@ __device__ __forceinline__ float2 twiddle(float2 a, float2 w_fwd)
     return DIR < 0 ? cmul(a, w_fwd) : cmulc(a, w_fwd);
 }
 
-// cos(2 pi m / 16) and sin(2 pi m / 16), m in [0, 16).
-__device__ __forceinline__ constexpr float cos16(int m)
+// cos(2 pi m / 32) and sin(2 pi m / 32), m in [0, 32).
+__device__ __forceinline__ constexpr float cos32(int m)
 {
-    constexpr float c[16] = {1.0f, 0.92387953251128675613f, 0.70710678118654752440f, 0.38268343236508977173f,
-                             0.0f, -0.38268343236508977173f, -0.70710678118654752440f, -0.92387953251128675613f,
-                             -1.0f, -0.92387953251128675613f, -0.70710678118654752440f, -0.38268343236508977173f,
-                             0.0f, 0.38268343236508977173f, 0.70710678118654752440f, 0.92387953251128675613f};
-    return c[m & 15];
+    constexpr float c[8] = {1.0f,
+                            0.98078528040323044913f,
+                            0.92387953251128675613f,
+                            0.83146961230254523708f,
+                            0.70710678118654752440f,
+                            0.55557023301960222474f,
+                            0.38268343236508977173f,
+                            0.19509032201612826785f};
+    // quarter-wave symmetry: cos on [0, 2 pi) from its first quarter
+    const int q = (m & 31) >> 3, r = m & 7;
+    return q == 0 ? c[r] : q == 1 ? (r == 0 ? 0.0f : -c[8 - r]) : q == 2 ? -c[r] : (r == 0 ? 0.0f : c[8 - r]);
 }
-__device__ __forceinline__ constexpr float sin16(int m) { return cos16(m + 12); }
+__device__ __forceinline__ constexpr float sin32(int m) { return cos32(m + 24); }
 
-// a * exp(DIR 2 pi i M / R) with M, R compile-time (R divides 16).
+// a * exp(DIR 2 pi i M / R) with M, R compile-time (R divides 32).
 template <int R, int M, int DIR>
 __device__ __forceinline__ float2 rot(float2 a)
 {
-    constexpr int m16 = ((M % R) * (16 / R)) & 15;  // same angle on the 16-grid
-    if constexpr (m16 == 0) {
+    static_assert(32 % R == 0, "rotation grid is the 32nd roots of unity");
+    constexpr int m32 = ((M % R) * (32 / R)) & 31;  // same angle on the 32-grid
+    if constexpr (m32 == 0) {
         return a;
-    } else if constexpr (m16 == 4) {
+    } else if constexpr (m32 == 8) {
         return mul_i<DIR>(a);
-    } else if constexpr (m16 == 8) {
+    } else if constexpr (m32 == 16) {
         return make_float2(-a.x, -a.y);
-    } else if constexpr (m16 == 12) {
+    } else if constexpr (m32 == 24) {
         return mul_i<-DIR>(a);
     } else {
-        constexpr float c = cos16(m16);
-        constexpr float s = DIR * sin16(m16);
+        constexpr float c = cos32(m32);
+        constexpr float s = DIR * sin32(m32);
         return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
     }
 }
@@ -180,6 +188,11 @@ struct Dft<8, DIR> {
 template <int DIR>
 struct Dft<16, DIR> {
     __device__ __forceinline__ static void run(float2* a) { DftSplit<4, 4, DIR>::run(a); }
+};
+
+template <int DIR>
+struct Dft<32, DIR> {
+    __device__ __forceinline__ static void run(float2* a) { DftSplit<4, 8, DIR>::run(a); }
 };
 
 // Runtime radix dispatch for the generic kernels.

@@ -22,8 +22,8 @@ namespace fft3d {
 
 constexpr int pick_radix(int rem, int E)
 {
-    constexpr int order[6] = {16, 8, 4, 2, 5, 3};
-    for (int i = 0; i < 6; ++i)
+    constexpr int order[7] = {32, 16, 8, 4, 2, 5, 3};
+    for (int i = 0; i < 7; ++i)
         if (E % order[i] == 0 && rem % order[i] == 0) return order[i];
     return 0;
 }
@@ -87,8 +87,8 @@ struct RowExchange {
 };
 
 // Twiddle inputs 1..R-1 of a radix-R butterfly by W^{k*base} (table units).
-// Only the powers 1, 2, 4 (and 8) are read from the FP32 table; the others
-// are products of two or three of them (each product adds one FP32 rounding).
+// Only the powers 1, 2, 4 (8, 16) are read from the FP32 table; the others
+// are products of two to four of them (each product adds one FP32 rounding).
 template <int R, int DIR>
 __device__ __forceinline__ void twiddle_inputs(float2* a, const float2* __restrict__ tw, int base)
 {
@@ -110,6 +110,23 @@ __device__ __forceinline__ void twiddle_inputs(float2* a, const float2* __restri
         a[2] = twiddle<DIR>(a[2], w2);
         a[3] = twiddle<DIR>(a[3], cmul(w1, w2));
         a[4] = twiddle<DIR>(a[4], w4);
+    } else if constexpr (R == 32) {
+        // powers 1, 2, 4, 8, 16 from the table, the rest as products
+        float2 w[32];
+        w[1] = w1;
+        w[2] = __ldg(&tw[2 * base]);
+        w[4] = __ldg(&tw[4 * base]);
+        w[8] = __ldg(&tw[8 * base]);
+        w[16] = __ldg(&tw[16 * base]);
+        w[3] = cmul(w[1], w[2]);
+#pragma unroll
+        for (int k = 5; k < 8; ++k) w[k] = cmul(w[k - 4], w[4]);
+#pragma unroll
+        for (int k = 9; k < 16; ++k) w[k] = cmul(w[k - 8], w[8]);
+#pragma unroll
+        for (int k = 17; k < 32; ++k) w[k] = cmul(w[k - 16], w[16]);
+#pragma unroll
+        for (int k = 1; k < 32; ++k) a[k] = twiddle<DIR>(a[k], w[k]);
     } else if constexpr (R == 8 || R == 16) {
         const float2 w2 = __ldg(&tw[2 * base]);
         const float2 w4 = __ldg(&tw[4 * base]);

@@ -181,6 +181,31 @@ def test_fused_plane_batched(cuda_lib):
         assert rel_l2(y[b], oracle.c2r3d(Y[b].astype(np.complex128), 32)) <= TOL
 
 
+@pytest.mark.parametrize("shape", [(32, 32, 32), (2, 32, 32, 32), (300, 128, 128), (128, 128, 128), (64, 256, 256),
+                                   (4, 512, 512), (40, 512, 512)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_cluster_plane_vs_oracle(cuda_lib, shape):
+    """Shapes with a cluster plane kernel (rows + n1 columns of each plane in
+    one cluster's distributed shared memory), including more planes than
+    co-resident clusters and a batch of two: both directions match the oracle."""
+    n0, n1, n2 = shape[-3:]
+    f = cuda_lib.FFT3D_FLAG_CLUSTER_PLANE
+    x32 = synth.uniform_field(shape, seed=65).astype(np.float32)
+    X = gpu_r2c(cuda_lib, x32, flags=f)
+    lead = shape[:-3]
+    Y = random_half_spectrum((int(np.prod(lead, dtype=int)) * n0, n1, n2 // 2 + 1), seed=66)
+    Y = Y.reshape(lead + (n0, n1, n2 // 2 + 1))
+    y = gpu_c2r(cuda_lib, Y, n2, flags=f)
+    for b in range(1 if len(shape) == 3 else shape[0]):
+        xb = x32 if len(shape) == 3 else x32[b]
+        Xb = X if len(shape) == 3 else X[b]
+        Yb = Y if len(shape) == 3 else Y[b]
+        yb = y if len(shape) == 3 else y[b]
+        assert rel_l2(Xb, oracle.r2c3d(xb.astype(np.float64))) <= TOL
+        assert rel_l2(yb, oracle.c2r3d(Yb.astype(np.complex128), n2)) <= TOL
+    assert "cluster-plane" in cuda_lib.Plan(n0, n1, n2, flags=f).describe()
+
+
 def test_bounded_wait_gives_up_without_hanging(cuda_lib):
     """Failure detection without a GPU fault: with the test hook, the
     producers of plane 0 never report, so the consumers' bounded waits give up
