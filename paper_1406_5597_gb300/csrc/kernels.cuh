@@ -503,7 +503,20 @@ __global__ void __launch_bounds__(W*(L / E)) col_pipe_kernel(ColArgs a, long lon
 // ---------------------------------------------------------------------------
 constexpr unsigned kMbarMaxTries = 1u << 20;
 
-template <int L, int E, int DIR, int W, int STAGES, int PF = 0, bool PAIR = false>
+// XB: a dedicated exchange buffer next to the ring, so reading the slot and
+// the first exchange write need no barrier between them, and the next tile's
+// barrier orders the buffer's reuse (two CTA barriers per tile with a single
+// exchange instead of four).  Used where the ring alone already limits the
+// SM to one CTA and the buffer still fits.
+template <int L, int E, int W, int STAGES, bool PAIR>
+constexpr bool col_tma_xbuf()
+{
+    constexpr size_t ring = (size_t)STAGES * L * (PAIR ? W + 2 : W) * 8 + 64;
+    return ring > 113 * 1024 && ring + (size_t)L * W * 8 <= 227 * 1024;
+}
+
+template <int L, int E, int DIR, int W, int STAGES, int PF = 0, bool PAIR = false,
+          bool XB = col_tma_xbuf<L, E, W, STAGES, PAIR>()>
 __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constant__ CUtensorMap tmap, ColArgs a,
                                                            long long ntiles)
 {
@@ -516,8 +529,10 @@ __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constan
     static_assert(!PAIR || (L % 2 == 0 && W % 2 == 0), "row pairs need even L and W");
     constexpr int WS = PAIR ? W + 2 : W;  // slot row width (complex values)
     constexpr unsigned TILE_BYTES = (unsigned)L * WS * sizeof(float2);
+    constexpr size_t XBYTES = XB ? (size_t)L * W * sizeof(float2) : 0;
     float2* ring = reinterpret_cast<float2*>(smraw);
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smraw + (size_t)STAGES * TILE_BYTES);
+    float2* xbuf = reinterpret_cast<float2*>(smraw + (size_t)STAGES * TILE_BYTES);
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smraw + (size_t)STAGES * TILE_BYTES + XBYTES);
     const int c = threadIdx.x;
     const int t = threadIdx.y;
     const bool leader = (c == 0 && t == 0);
@@ -569,6 +584,10 @@ __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constan
 #pragma unroll
         for (int s = 0; s < STAGES - 1; ++s) issue(blockIdx.x + (long long)s * gridDim.x, s);
     }
+    // the butterfly positions of a thread are the same in every tile: its
+    // twiddles are formed once
+    TwCache<L, E> twc;
+    twc.fill(a.tw, t);
     int stage = 0;
     unsigned phase = 0;
     int consumed[STAGES];
@@ -589,7 +608,13 @@ __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constan
         const bool active = (c0 + c) < a.C;
         float2* buf = ring + (size_t)stage * L * WS;
         float2 v[E];
-        if constexpr (PAIR) {
+        if constexpr (PAIR && T % 2 == 0) {
+            // row parity is the thread's own (t + T*m has the parity of t):
+            // even rows from the box at c0, odd rows from the box at c0 - 1
+            const float2* src = (t & 1) ? buf + (L / 2) * WS + c + 1 : buf + c;
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = src[((t >> 1) + (T / 2) * m) * WS];
+        } else if constexpr (PAIR) {
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 const int j = t + T * m;  // even rows: box from c0; odd rows: box from c0 - 1
@@ -599,9 +624,12 @@ __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constan
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = buf[(t + T * m) * W + c];
         }
-        __syncthreads();  // the slot now serves as the exchange buffer
-        ColExchange exch{buf, W, c};
-        fft_group<L, E, DIR>(v, t, a.tw, exch);
+        if constexpr (XB) {
+            fft_group<L, E, DIR>(v, t, twc, ColExchangeNoTail{xbuf, W, c});
+        } else {
+            __syncthreads();  // the slot now serves as the exchange buffer
+            fft_group<L, E, DIR>(v, t, twc, ColExchange{buf, W, c});
+        }
         fence_proxy_async_smem();  // order this thread's shared accesses before the slot's next bulk copy
         if (active) {
             float2* dst = (a.dst ? a.dst : a.data) + b * a.Bs + c0 + c;
@@ -744,7 +772,9 @@ inline cudaError_t launch_col_tma(const ColArgs& a, const CUtensorMap& map, cuda
 {
     constexpr int T = L / E;
     constexpr int WS = PAIR ? W + 2 : W;
-    const size_t smem = (size_t)STAGES * L * WS * sizeof(float2) + STAGES * sizeof(unsigned long long);
+    constexpr bool XB = col_tma_xbuf<L, E, W, STAGES, PAIR>();
+    const size_t smem = (size_t)STAGES * L * WS * sizeof(float2) + (XB ? (size_t)L * W * sizeof(float2) : 0) +
+                        STAGES * sizeof(unsigned long long);
     auto k = col_tma_kernel<L, E, DIR, W, STAGES, PF, PAIR>;
     static int per_sm = 0;
     static int sms = 0;
