@@ -328,7 +328,8 @@ def main():
         for name, flags in (("explicit_transpose", fft3d.FFT3D_FLAG_EXPLICIT_TRANSPOSE),
                             ("explicit_transpose_back", fft3d.FFT3D_FLAG_EXPLICIT_TRANSPOSE
                              | fft3d.FFT3D_FLAG_TRANSPOSE_BACK),
-                            ("fused_plane", fft3d.FFT3D_FLAG_FUSED_PLANE)):
+                            ("fused_plane", fft3d.FFT3D_FLAG_FUSED_PLANE),
+                            ("cluster_plane", fft3d.FFT3D_FLAG_CLUSTER_PLANE)):
             vp = fft3d.Plan(n0, n1, n2, flags=flags)
 
             def vstep(vp=vp):
@@ -339,7 +340,7 @@ def main():
                 vstep()
             vms = time_steps(vstep, stream, max(5, args.steps // 2)) / max(5, args.steps // 2)
             variants[name] = {"ms_per_step": vms, "gbs_effective": nbytes / (vms * 1e-3) / 1e9,
-                              "slowdown_vs_transpose_free": vms / ms}
+                              "slowdown_vs_transpose_free": vms / ms, "plan": vp.describe()}
             vp.close()
         line["variants"] = variants
 

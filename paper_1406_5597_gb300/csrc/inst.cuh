@@ -8,10 +8,10 @@
 #define FFT3D_COL(L, E, W) E, W, &fft3d::launch_col<L, E, W, -1>, &fft3d::launch_col<L, E, W, 1>
 #define FFT3D_NO_TMA 0, 0, nullptr, nullptr, nullptr, nullptr
 // TMA-fed persistent column kernel: E, W, ring stages, L2 prefetch distance;
-// the row-pair variant (odd axis stride) uses PST stages
-#define FFT3D_TMA(L, E, W, ST, PF, PST)                                                                   \
+// the row-pair variant (odd axis stride) uses PST stages and prefetch distance PPF
+#define FFT3D_TMA(L, E, W, ST, PF, PST, PPF)                                                              \
     E, W, &fft3d::launch_col_tma<L, E, W, ST, -1, PF>, &fft3d::launch_col_tma<L, E, W, ST, 1, PF>,        \
-        &fft3d::launch_col_tma<L, E, W, PST, -1, PF, true>, &fft3d::launch_col_tma<L, E, W, PST, 1, PF, true>
+        &fft3d::launch_col_tma<L, E, W, PST, -1, PPF, true>, &fft3d::launch_col_tma<L, E, W, PST, 1, PPF, true>
 #define FFT3D_TMA_NOPAIR(L, E, W, ST, PF) \
     E, W, &fft3d::launch_col_tma<L, E, W, ST, -1, PF>, &fft3d::launch_col_tma<L, E, W, ST, 1, PF>, nullptr, nullptr
 // warp-resident rows (T = L/E <= 32), ROWS rows per CTA

@@ -47,9 +47,14 @@ __global__ void __launch_bounds__(MAXT) col_kernel(ColArgs a, int W)
     fft_group<L, E, DIR>(v, t, a.tw, ex);
     if (active) {
         float2* out = (a.dst ? a.dst : a.data) + b * a.Bs + c0 + c;
+        if (a.mask23 == 0 && a.scale == 1.0f) {
 #pragma unroll
-        for (int m = 0; m < E; ++m)
-            out[(long long)(t + T * m) * a.S] = cscale(v[m], col_out_factor(t + T * m, L, a.scale, a.mask23));
+            for (int m = 0; m < E; ++m) out[(long long)(t + T * m) * a.S] = v[m];
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m)
+                out[(long long)(t + T * m) * a.S] = cscale(v[m], col_out_factor(t + T * m, L, a.scale, a.mask23));
+        }
     }
 }
 
@@ -537,9 +542,9 @@ __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constan
     const int t = threadIdx.y;
     const bool leader = (c == 0 && t == 0);
     const long long ctiles = (a.C + W - 1) / W;
-    int uses[STAGES];  // leader: loads issued per slot (parity bookkeeping for the drain)
-#pragma unroll
-    for (int s = 0; s < STAGES; ++s) uses[s] = 0;
+    // leader: copies issued so far; the k-th goes to slot k % STAGES with
+    // phase parity (k / STAGES) & 1 (bookkeeping for the drain)
+    long long n_issued = 0;
 
     if (leader) {
         prefetch_tensormap(&tmap);
@@ -564,7 +569,7 @@ __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constan
                 tma_load_2d(slot + (size_t)(L / 2) * WS + (size_t)k * BOXR * WS, &tmap, (int)(2 * (a.S + c0 - 1)), y,
                             &bars[s]);
         }
-        ++uses[s];
+        ++n_issued;
         if constexpr (PF > 0) {  // warm L2 with the tile PF ring-lengths further on
             const long long pt = tile + (long long)PF * gridDim.x;
             if (pt < ntiles) {
@@ -590,9 +595,7 @@ __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constan
     twc.fill(a.tw, t);
     int stage = 0;
     unsigned phase = 0;
-    int consumed[STAGES];
-#pragma unroll
-    for (int s = 0; s < STAGES; ++s) consumed[s] = 0;
+    long long n_consumed = 0;
     bool failed = false;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const bool ok = mbar_wait_bounded(&bars[stage], phase, kMbarMaxTries);
@@ -600,7 +603,7 @@ __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constan
             failed = true;
             break;
         }
-        ++consumed[stage];
+        ++n_consumed;
         // the slot consumed in the previous iteration is free again: refill it
         if (leader) issue(tile + (long long)(STAGES - 1) * gridDim.x, (stage + STAGES - 1) % STAGES);
         const long long b = tile / ctiles;
@@ -633,9 +636,14 @@ __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constan
         fence_proxy_async_smem();  // order this thread's shared accesses before the slot's next bulk copy
         if (active) {
             float2* dst = (a.dst ? a.dst : a.data) + b * a.Bs + c0 + c;
+            if (a.mask23 == 0 && a.scale == 1.0f) {
 #pragma unroll
-            for (int m = 0; m < E; ++m)
-                dst[(long long)(t + T * m) * a.S] = cscale(v[m], col_out_factor(t + T * m, L, a.scale, a.mask23));
+                for (int m = 0; m < E; ++m) dst[(long long)(t + T * m) * a.S] = v[m];
+            } else {
+#pragma unroll
+                for (int m = 0; m < E; ++m)
+                    dst[(long long)(t + T * m) * a.S] = cscale(v[m], col_out_factor(t + T * m, L, a.scale, a.mask23));
+            }
         }
         if (++stage == STAGES) {
             stage = 0;
@@ -645,9 +653,8 @@ __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constan
     if (failed && leader) {
         atomicOr(a.status, kStatusTimeout);
         // drain: wait (bounded) for every copy issued but not consumed
-#pragma unroll
-        for (int s = 0; s < STAGES; ++s)
-            for (int u = consumed[s]; u < uses[s]; ++u) mbar_wait_bounded(&bars[s], (unsigned)(u & 1), kMbarMaxTries);
+        for (long long k = n_consumed; k < n_issued; ++k)
+            mbar_wait_bounded(&bars[k % STAGES], (unsigned)((k / STAGES) & 1), kMbarMaxTries);
     }
 }
 
