@@ -68,10 +68,11 @@ def measured_peak_hbm():
 
 
 def kernel_source_hash():
+    """Hash of the device-code sources (.cu, .cuh, .h; host-only .cpp excluded)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1406_5597_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+        if name.endswith((".cu", ".cuh", ".h")):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode())
                 h.update(f.read())

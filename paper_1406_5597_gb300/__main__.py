@@ -1,0 +1,46 @@
+"""One-shot driver: a plan, one forward r2c and one inverse c2r on seeded
+random data on the current CUDA device, through the C ABI.
+
+    python -m paper_1406_5597_gb300 --shape 512,512,512 [--flags 0x40] [--dtype f32|bf16x3|f16]
+
+Prints the plan description and the round-trip relative L2 error
+(c2r(r2c(x)) / N against x).  Useful as the target of a profiler run: it
+launches exactly the kernels of one transform pair.
+"""
+import argparse
+
+import torch
+
+from . import FFT3D_F32, FFT3D_F32_TC_BF16X3, FFT3D_F32_TC_F16, Plan, load
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--shape", default="512,512,512", help="n0,n1,n2")
+    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--flags", type=lambda v: int(v, 0), default=0, help="FFT3D_FLAG_* bits")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16x3", "f16"])
+    ap.add_argument("--seed", type=int, default=1408)
+    args = ap.parse_args()
+    n0, n1, n2 = (int(v) for v in args.shape.split(","))
+    dtype = {"f32": FFT3D_F32, "bf16x3": FFT3D_F32_TC_BF16X3, "f16": FFT3D_F32_TC_F16}[args.dtype]
+    load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(args.seed)
+    lead = (args.batch,) if args.batch > 1 else ()
+    x = torch.randn(lead + (n0, n1, n2), device=dev, generator=gen)
+    X = torch.empty(lead + (n0, n1, n2 // 2 + 1), dtype=torch.complex64, device=dev)
+    y = torch.empty_like(x)
+    plan = Plan(n0, n1, n2, dtype, args.batch, args.flags)
+    s = torch.cuda.current_stream(dev).cuda_stream
+    plan.r2c(x.data_ptr(), X.data_ptr(), s)
+    plan.c2r(X.data_ptr(), y.data_ptr(), s)
+    torch.cuda.synchronize(dev)
+    err = float((y / (n0 * n1 * n2) - x).norm() / x.norm())
+    print(f"{plan.describe()}; round trip rel-L2 {err:.3e}")
+    plan.close()
+
+
+if __name__ == "__main__":
+    main()
