@@ -192,6 +192,23 @@ int fft3d_get_choices(fft3d_handle plan, int* choices5);
 int fft3d_set_choices(fft3d_handle plan, const int* choices5);
 
 /*
+ * Plane form (the 2D transform of every n0-plane, Sec. 2.1 step 1): 0 = a
+ * row pass and an n1 column pass; C > 0 = one cluster plane pass that holds
+ * each plane in the shared memory of a C-CTA thread-block cluster (C = 1: one
+ * CTA).  fft3d_autotune (plans without FFT3D_FLAG_THREE_PASS, _GENERIC,
+ * _EXPLICIT_TRANSPOSE, _FUSED_PLANE, FP32) times both forms over a whole
+ * r2c + c2r, every instantiated cluster size of the shape, and keeps the
+ * fastest.  fft3d_get_plane_choice returns the plan's current C (>= 0), or
+ * minus the status on error.  fft3d_set_plane_choice sets it: 0 always works;
+ * C > 0 needs an instantiated cluster kernel of the plan's (n2/2, n1) with that
+ * cluster size (else FFT3D_ERR_UNSUPPORTED_SIZE, plan unchanged) and a plan
+ * the form applies to (else FFT3D_ERR_INVALID_ARG).  Host only; set it before
+ * the plan's first use in a captured graph.
+ */
+int fft3d_get_plane_choice(fft3d_handle plan);
+int fft3d_set_plane_choice(fft3d_handle plan, int cluster);
+
+/*
  * Grouped transforms of uneven sizes (e.g. several grids of a multi-resolution
  * run).  dims: ngroups x 3 ints (n0, n1, n2) (host); counts: fields per group
  * (host).  Group i is a plan of batch counts[i]; fft3d_group_r2c / c2r take

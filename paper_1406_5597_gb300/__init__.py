@@ -74,6 +74,8 @@ _SIGS = {
     "fft3d_autotune": ([_P, _P, _P, _I, _P], _I),
     "fft3d_get_choices": ([_P, _P], _I),
     "fft3d_set_choices": ([_P, _P], _I),
+    "fft3d_get_plane_choice": ([_P], _I),
+    "fft3d_set_plane_choice": ([_P, _I], _I),
     "fft3d_plan_group": ([_P, _P, _I, _I], _P),
     "fft3d_group_plan_at": ([_P, _I], _P),
     "fft3d_group_r2c": ([_P, _P, _P, _P], _I),
@@ -301,6 +303,18 @@ def fft3d_set_choices(plan, choices):
         raise ValueError("five choices: w0, w1, rows, tma0, tma1")
     c = (ctypes.c_int * 5)(*choices)
     return load().fft3d_set_choices(_v(plan), c)
+
+
+def fft3d_get_plane_choice(plan):
+    """Cluster size of the plan's plane pass (0: separate row and n1 passes)."""
+    c = load().fft3d_get_plane_choice(_v(plan))
+    if c < 0:
+        raise Fft3dError(-c, "fft3d_get_plane_choice")
+    return c
+
+
+def fft3d_set_plane_choice(plan, cluster):
+    return load().fft3d_set_plane_choice(_v(plan), int(cluster))
 
 
 def _ptr_array(ptrs):

@@ -415,6 +415,25 @@ cudaError_t run_plane(fft3d_plan_s* p, int dir, const void* in, void* out, cudaS
     return dir < 0 ? p->plane->fwd(a, s) : p->plane->inv(a, s);
 }
 
+// The cluster plane kernel of shape (n2/2 = LR, n1 = LC) with cluster size C
+// (C = 0: the shape's default, the first listed), or nullptr.
+const CPlaneEntry* cplane_for(int LR, int LC, int C)
+{
+    int nc = 0;
+    const CPlaneEntry* ce = cplane_entries(&nc);
+    for (int i = 0; i < nc; ++i)
+        if (ce[i].LR == LR && ce[i].LC == LC && (C == 0 || ce[i].C == C)) return &ce[i];
+    return nullptr;
+}
+
+// The plan may replace its row and n1 passes by a cluster plane pass.
+bool cplane_allowed(const fft3d_plan_s* p)
+{
+    return p->dtype == FFT3D_F32 && !p->plane &&
+           !(p->flags & (FFT3D_FLAG_THREE_PASS | FFT3D_FLAG_GENERIC | FFT3D_FLAG_EXPLICIT_TRANSPOSE |
+                         FFT3D_FLAG_FUSED_PLANE));
+}
+
 // The cluster plane pass (rows + n1 columns of every plane, one cluster per plane).
 cudaError_t run_cplane(fft3d_plan_s* p, int dir, const void* in, void* out, cudaStream_t s)
 {
@@ -596,13 +615,7 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
             }
         }
     }
-    if ((flags & FFT3D_FLAG_CLUSTER_PLANE) && !p->plane &&
-        !(flags & (FFT3D_FLAG_THREE_PASS | FFT3D_FLAG_GENERIC | FFT3D_FLAG_EXPLICIT_TRANSPOSE))) {
-        int nc = 0;
-        const CPlaneEntry* ce = cplane_entries(&nc);
-        for (int i = 0; i < nc; ++i)
-            if (ce[i].LR == n2 / 2 && ce[i].LC == n1) p->cplane = &ce[i];
-    }
+    if ((flags & FFT3D_FLAG_CLUSTER_PLANE) && cplane_allowed(p)) p->cplane = cplane_for(n2 / 2, n1, 0);
     {
         // energy scratch for nbins up to the largest shell of the shape
         const double kmax = std::sqrt((double)(n0 / 2) * (n0 / 2) + (double)(n1 / 2) * (n1 / 2) +
@@ -984,6 +997,26 @@ int fft3d_set_choices(fft3d_handle p, const int* c)
     return FFT3D_OK;
 }
 
+int fft3d_get_plane_choice(fft3d_handle p)
+{
+    if (!p) return -fail(FFT3D_ERR_INVALID_ARG);
+    return p->cplane ? p->cplane->C : 0;
+}
+
+int fft3d_set_plane_choice(fft3d_handle p, int cluster)
+{
+    if (!p || cluster < 0) return fail(FFT3D_ERR_INVALID_ARG);
+    if (cluster == 0) {
+        p->cplane = nullptr;
+        return FFT3D_OK;
+    }
+    if (!cplane_allowed(p)) return fail(FFT3D_ERR_INVALID_ARG);
+    const CPlaneEntry* e = cplane_for(p->n2 / 2, p->n1, cluster);
+    if (!e) return fail(FFT3D_ERR_UNSUPPORTED_SIZE);
+    p->cplane = e;
+    return FFT3D_OK;
+}
+
 int fft3d_autotune(fft3d_handle p, float* real, void* cplx, int reps, void* stream)
 {
     if (!p || !real || !cplx) return fail(FFT3D_ERR_INVALID_ARG);
@@ -1043,6 +1076,22 @@ int fft3d_autotune(fft3d_handle p, float* real, void* cplx, int reps, void* stre
         }
         p->choice_w0 = pick_w;
         p->choice_tma = pick_tma;
+    }
+    // plane form: separate row and n1 passes, or a cluster plane kernel of
+    // each instantiated cluster size, timed over a whole r2c + c2r
+    if (cplane_allowed(p) && cplane_for(p->n2 / 2, p->n1, 0)) {
+        int nc = 0;
+        const CPlaneEntry* ce = cplane_entries(&nc);
+        const CPlaneEntry* best_e = nullptr;
+        p->cplane = nullptr;
+        float best = time_pass([&] { fft3d_r2c(p, real, cplx, stream); fft3d_c2r(p, cplx, real, stream); }, reps, s);
+        for (int i = 0; i < nc; ++i) {
+            if (ce[i].LR != p->n2 / 2 || ce[i].LC != p->n1) continue;
+            p->cplane = &ce[i];
+            const float t = time_pass([&] { fft3d_r2c(p, real, cplx, stream); fft3d_c2r(p, cplx, real, stream); }, reps, s);
+            if (t < best) best = t, best_e = &ce[i];
+        }
+        p->cplane = best_e;
     }
     p->profiling = prof;
     return cudaGetLastError() == cudaSuccess ? FFT3D_OK : fail(FFT3D_ERR_CUDA);

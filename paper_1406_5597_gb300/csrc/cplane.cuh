@@ -117,6 +117,8 @@ struct CPlaneGeom {
     static constexpr int KPC = RC / C;                     // k' rows per CTA in the radix-C step
     static constexpr int NX = KPC * H;                     // radix-C items per CTA
     static constexpr int XI = NX / NT;                     // items every thread takes (the rest: a tail)
+    static constexpr int XP0 = XI < 16 / C ? XI : 16 / C;  // inverse: items loaded one plane ahead
+    static constexpr int XPRE = XP0 > 0 ? XP0 : (XI > 0 ? 1 : 0);  // (at most 16 values in registers)
     static constexpr int SLAB = RC * SH;                   // complex values
     static constexpr unsigned ROW_BYTES = LR * sizeof(float2);
     static constexpr unsigned STAGE_BYTES = RPR * ROW_BYTES;
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(NT, MINB) cplane_kernel(CPlaneArgs a)
 {
     using G = CPlaneGeom<LR, ER, LC, C, NT>;
     constexpr int H = G::H, RC = G::RC, SH = G::SH, TR = G::TR, RPR = G::RPR;
-    constexpr int EC = G::EC, TC = G::TC, GC = G::GC, KPC = G::KPC, NX = G::NX, XI = G::XI;
+    constexpr int EC = G::EC, TC = G::TC, GC = G::GC, KPC = G::KPC, NX = G::NX, XI = G::XPRE;
     extern __shared__ __align__(1024) unsigned char smraw[];
     float2* slab = reinterpret_cast<float2*>(smraw);
     const unsigned rank = cluster_ctarank();
@@ -273,9 +275,9 @@ __global__ void __launch_bounds__(NT, MINB) cplane_kernel(CPlaneArgs a)
             cluster_sync_all();  // no slab is refilled while another CTA may still read it
         }
     } else {
-        // Inverse.  The spectrum values of the radix-C step are loaded into
-        // registers one plane ahead (XI items per thread), across the barrier
-        // that ends the previous plane.
+        // Inverse.  The spectrum values of the first XI radix-C items of a
+        // thread are loaded into registers one plane ahead, across the
+        // barrier that ends the previous plane; the others in the step itself.
         const float2* in = reinterpret_cast<const float2*>(a.in);
         float2 pre[XI > 0 ? XI : 1][C];
         auto load_items = [&](long long p) {

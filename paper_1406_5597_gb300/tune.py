@@ -1,9 +1,9 @@
 """Autotuning cache ("wisdom"): kernel shape choices per GPU and transform.
 
 fft3d_autotune (C) times the candidate shapes of every pass on the caller's
-buffers and keeps the fastest; this module stores the chosen five integers
-{w0, w1, rows, tma0, tma1} in a JSON file so later plans of the same GPU model and
-shape reuse them without tuning.  File: $FFT3D_TUNE_CACHE, else
+buffers and keeps the fastest; this module stores the chosen six integers
+{w0, w1, rows, tma0, tma1, plane cluster size} in a JSON file so later plans of
+the same GPU model and shape reuse them without tuning.  File: $FFT3D_TUNE_CACHE, else
 ~/.cache/fft3d_wisdom.json.
 """
 from __future__ import annotations
@@ -13,7 +13,7 @@ import os
 import tempfile
 
 from . import (FFT3D_F32, FFT3D_OK, Fft3dError, Plan, fft3d_autotune, fft3d_get_choices,
-               fft3d_set_choices)
+               fft3d_get_plane_choice, fft3d_set_choices, fft3d_set_plane_choice)
 
 
 def cache_path() -> str:
@@ -56,10 +56,14 @@ def tuned_plan(n0, n1, n2, batch=1, dtype=FFT3D_F32, flags=0, reps=5, path=None,
     gpu = torch.cuda.get_device_name()
     key = cache_key(gpu, (n0, n1, n2), batch, dtype, flags)
     cached = None if retune else load_cache(path).get(key)
-    if cached is not None and len(cached) == 5:
-        st = fft3d_set_choices(plan.handle, cached)
+    if cached is not None and len(cached) in (5, 6):
+        st = fft3d_set_choices(plan.handle, cached[:5])
         if st != FFT3D_OK:
             raise Fft3dError(st, "fft3d_set_choices")
+        if len(cached) == 6:
+            st = fft3d_set_plane_choice(plan.handle, cached[5])
+            if st != FFT3D_OK:
+                raise Fft3dError(st, "fft3d_set_plane_choice")
         return plan, False
     real = torch.empty(batch * n0 * n1 * n2, dtype=torch.float32, device="cuda").normal_()
     cplx = torch.empty(batch * n0 * n1 * (n2 // 2 + 1), dtype=torch.complex64, device="cuda")
@@ -67,5 +71,5 @@ def tuned_plan(n0, n1, n2, batch=1, dtype=FFT3D_F32, flags=0, reps=5, path=None,
                         torch.cuda.current_stream().cuda_stream)
     if st != FFT3D_OK:
         raise Fft3dError(st, "fft3d_autotune")
-    store_cache({key: fft3d_get_choices(plan.handle)}, path)
+    store_cache({key: fft3d_get_choices(plan.handle) + [fft3d_get_plane_choice(plan.handle)]}, path)
     return plan, True

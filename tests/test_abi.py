@@ -67,5 +67,8 @@ def test_null_handles(lib):
     assert fft3d.fft3d_set_workspace(None, 0) == fft3d.FFT3D_ERR_INVALID_ARG
     assert fft3d.fft3d_launches_per_call(None) == fft3d.FFT3D_ERR_INVALID_ARG
     fft3d.fft3d_destroy(None)
+    assert fft3d.fft3d_set_plane_choice(None, 2) == fft3d.FFT3D_ERR_INVALID_ARG
+    with pytest.raises(fft3d.Fft3dError):
+        fft3d.fft3d_get_plane_choice(None)
     buf = ctypes.create_string_buffer(8)
     assert lib.fft3d_describe(None, buf, 8) == fft3d.FFT3D_ERR_INVALID_ARG

@@ -208,6 +208,58 @@ def test_cluster_plane_vs_oracle(cuda_lib, shape):
     assert "cluster-plane" in cuda_lib.Plan(n0, n1, n2, flags=f).describe()
 
 
+def _plan_r2c_c2r(lib, plan, x32, Y64, n2):
+    s = torch.cuda.current_stream().cuda_stream
+    xd = torch.from_numpy(np.ascontiguousarray(x32)).cuda()
+    X = torch.empty(Y64.shape, dtype=torch.complex64, device="cuda")
+    plan.r2c(xd.data_ptr(), X.data_ptr(), s)
+    Yd = torch.from_numpy(np.ascontiguousarray(Y64)).cuda()
+    y = torch.empty(x32.shape, dtype=torch.float32, device="cuda")
+    plan.c2r(Yd.data_ptr(), y.data_ptr(), s)
+    torch.cuda.synchronize()
+    return X.cpu().numpy().astype(np.complex128), y.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("shape", [(9, 32, 32), (10, 64, 64), (5, 128, 128), (6, 256, 256), (3, 512, 512)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_plane_form_every_cluster_size_and_autotune(cuda_lib, shape):
+    """Every instantiated cluster size of a plane shape (set through
+    fft3d_set_plane_choice) and the separate-pass form match the oracle; the
+    autotuner picks one of them and the tuned plan still matches."""
+    lib = cuda_lib
+    n0, n1, n2 = shape
+    x32 = synth.uniform_field(shape, seed=67).astype(np.float32)
+    Y = random_half_spectrum((n0, n1, n2 // 2 + 1), seed=68)
+    Xo = oracle.r2c3d(x32.astype(np.float64))
+    yo = oracle.c2r3d(Y.astype(np.complex128), n2)
+    sizes = []
+    for C in (0, 1, 2, 4, 8, 16):
+        plan = lib.Plan(n0, n1, n2)
+        st = lib.fft3d_set_plane_choice(plan.handle, C)
+        if st != lib.FFT3D_OK:
+            assert st == lib.FFT3D_ERR_UNSUPPORTED_SIZE
+            assert lib.fft3d_get_plane_choice(plan.handle) == 0
+            continue
+        assert lib.fft3d_get_plane_choice(plan.handle) == C
+        assert ("cluster-plane" in plan.describe()) == (C > 0)
+        sizes.append(C)
+        X, y = _plan_r2c_c2r(lib, plan, x32, Y, n2)
+        assert rel_l2(X, Xo) <= TOL, C
+        assert rel_l2(y, yo) <= TOL, C
+    assert len(sizes) >= 2
+    plan = lib.Plan(n0, n1, n2)
+    real = torch.empty(n0 * n1 * n2, dtype=torch.float32, device="cuda").normal_()
+    cplx = torch.empty(n0 * n1 * (n2 // 2 + 1), dtype=torch.complex64, device="cuda")
+    assert lib.fft3d_autotune(plan.handle, real.data_ptr(), cplx.data_ptr(), 2,
+                              torch.cuda.current_stream().cuda_stream) == lib.FFT3D_OK
+    assert lib.fft3d_get_plane_choice(plan.handle) in sizes
+    X, y = _plan_r2c_c2r(lib, plan, x32, Y, n2)
+    assert rel_l2(X, Xo) <= TOL and rel_l2(y, yo) <= TOL
+    # forms the choice does not apply to
+    tp = lib.Plan(n0, n1, n2, flags=lib.FFT3D_FLAG_THREE_PASS)
+    assert lib.fft3d_set_plane_choice(tp.handle, sizes[-1]) == lib.FFT3D_ERR_INVALID_ARG
+
+
 def test_bounded_wait_gives_up_without_hanging(cuda_lib):
     """Failure detection without a GPU fault: with the test hook, the
     producers of plane 0 never report, so the consumers' bounded waits give up
