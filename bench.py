@@ -67,12 +67,17 @@ def measured_peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# the sources the row and column kernels of the 2^k lengths are built from
+KERNEL_SOURCES = ("args.h", "inst.cuh", "inst_256_512.cu", "inst_1024_2048.cu", "kernels.cuh", "radix.cuh",
+                  "stockham.cuh", "tma.cuh", "tma_host.h")
+
+
 def kernel_source_hash():
-    """Hash of the device-code sources (.cu, .cuh, .h; host-only .cpp excluded)."""
+    """Hash of the row / column kernels' device-code sources."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1406_5597_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name in KERNEL_SOURCES:
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode())
                 h.update(f.read())
