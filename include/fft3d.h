@@ -82,6 +82,13 @@ typedef enum {
                                              each plane in the distributed shared memory of a thread-block
                                              cluster (DRAM traffic of two passes; shapes with an
                                              instantiated cluster kernel only, else ignored) */
+#define FFT3D_FLAG_PADDED_REAL 0x80      /* real rows padded to 2*(n2/2+1) floats (FFTW's in-place layout: the
+                                             real array is batch x n0 x n1 x (n2+2) floats, the last two of
+                                             each row unused); fft3d_r2c / fft3d_c2r then also accept
+                                             in == out (the transform in place) */
+#define FFT3D_FLAG_PRESERVE_INPUT 0x100   /* fft3d_c2r leaves its input unchanged: its first column pass writes
+                                             into caller workspace (fft3d_workspace_bytes: batch*M complex)
+                                             and the rest runs there */
 #define FFT3D_FLAG_TEST_SKIP_ARRIVAL 0x10 /* testing only (with FUSED_PLANE): in the fused plane kernel the producers of
                                              plane 0 never report, so its consumers' bounded waits give
                                              up after about a millisecond; the call's output is then
@@ -104,8 +111,10 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
 
 /*
  * Forward r2c (Sec. 2; steps of Sec. 2.1 with the n0 pass of Sec. 2.2).
- * in:  batch*n0*n1*n2 floats (device), read only.
- * out: batch*n0*n1*H float2 (device); must not overlap in.
+ * in:  batch*n0*n1*n2 floats (device), read only; batch*n0*n1*(n2+2) floats
+ *      (rows padded to 2H) for FFT3D_FLAG_PADDED_REAL plans.
+ * out: batch*n0*n1*H float2 (device); must not overlap in, except that a
+ *      PADDED_REAL plan accepts out == in (in place, FFTW's layout).
  * For FFT3D_FLAG_EXPLICIT_TRANSPOSE plans without TRANSPOSE_BACK the result
  * is laid out batch x n1 x n0 x H ("axes 0 and 1 flipped", Sec. 2.1).
  * Both pointers 16-byte aligned.  Asynchronous on stream.
@@ -115,9 +124,16 @@ int fft3d_r2c(fft3d_handle plan, const float* in, void* out, void* stream);
 /*
  * Inverse c2r (Sec. 2; the forward steps in reverse order, Sec. 2.1).
  * in:  batch*n0*n1*H float2 (device); CLOBBERED (used as scratch, as FFTW's
- *      multi-dimensional c2r does).  For EXPLICIT_TRANSPOSE plans without
- *      TRANSPOSE_BACK it is read in the transposed batch x n1 x n0 x H layout.
- * out: batch*n0*n1*n2 floats (device); must not overlap in.
+ *      multi-dimensional c2r does) unless the plan has
+ *      FFT3D_FLAG_PRESERVE_INPUT (then read only; the plan needs workspace of
+ *      fft3d_workspace_bytes, which must not overlap in, else
+ *      FFT3D_ERR_NO_WORKSPACE / FFT3D_ERR_INVALID_ARG).  For EXPLICIT_TRANSPOSE
+ *      plans without TRANSPOSE_BACK it is read in the transposed
+ *      batch x n1 x n0 x H layout.
+ * out: batch*n0*n1*n2 floats (device), or batch*n0*n1*(n2+2) (rows padded to
+ *      2H, the last two floats of a row untouched) for PADDED_REAL plans; must
+ *      not overlap in, except that a PADDED_REAL plan without PRESERVE_INPUT
+ *      accepts out == in (in place).
  * Unnormalised.  Asynchronous on stream.
  */
 int fft3d_c2r(fft3d_handle plan, void* in, float* out, void* stream);

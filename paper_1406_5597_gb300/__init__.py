@@ -40,6 +40,8 @@ FFT3D_FLAG_GENERIC = 0x8
 FFT3D_FLAG_TEST_SKIP_ARRIVAL = 0x10
 FFT3D_FLAG_FUSED_PLANE = 0x20
 FFT3D_FLAG_CLUSTER_PLANE = 0x40
+FFT3D_FLAG_PADDED_REAL = 0x80
+FFT3D_FLAG_PRESERVE_INPUT = 0x100
 
 _lib = None
 _lock = threading.Lock()

@@ -341,20 +341,23 @@ cudaError_t launch_col_args(fft3d_plan_s* p, const Axis& a, int dir, const ColAr
     return dir < 0 ? a.spec->col_fwd(ca, w, s) : a.spec->col_inv(ca, w, s);
 }
 
+// dst: the result goes there (same layout) and data is only read; nullptr: in place
 cudaError_t run_col(fft3d_plan_s* p, const Axis& a, int dir, float2* data, long long S, long long C,
-                    long long nb, long long Bs, cudaStream_t s)
+                    long long nb, long long Bs, cudaStream_t s, float2* dst = nullptr)
 {
     if (a.L <= 1) return cudaSuccess;
     const bool n0axis = (&a == &p->ax0);
     ProfScope ps(p, n0axis ? (dir < 0 ? PASS_N0_FWD : PASS_N0_INV) : (dir < 0 ? PASS_N1_FWD : PASS_N1_INV), s);
-    ColArgs ca{data, S, C, nb, Bs, a.d_tw, 1.0f, p->d_status, nullptr, 0};
+    ColArgs ca{data, S, C, nb, Bs, a.d_tw, 1.0f, p->d_status, dst, 0};
     return launch_col_args(p, a, dir, ca, s);
 }
 
 cudaError_t run_row(fft3d_plan_s* p, int dir, const void* in, void* out, cudaStream_t s)
 {
     ProfScope ps(p, dir < 0 ? PASS_ROW_R2C : PASS_ROW_C2R, s);
-    RowArgs ra{in, out, (long long)p->batch * p->n0 * p->n1, p->ax2.d_tw, p->d_twpack};
+    // real rows: n2 floats, or 2H floats in the padded (in-place capable) layout
+    const long long rs = (p->flags & FFT3D_FLAG_PADDED_REAL) ? p->H : p->n2 / 2;
+    RowArgs ra{in, out, (long long)p->batch * p->n0 * p->n1, p->ax2.d_tw, p->d_twpack, rs};
     if (uses_generic(p, p->ax2, true)) return generic_row(ra, p->ax2.gen, dir, s);
     return dir < 0 ? p->ax2.spec->r2c(ra, p->choice_rows, s) : p->ax2.spec->c2r(ra, p->choice_rows, s);
 }
@@ -431,7 +434,7 @@ bool cplane_allowed(const fft3d_plan_s* p)
 {
     return p->dtype == FFT3D_F32 && !p->plane &&
            !(p->flags & (FFT3D_FLAG_THREE_PASS | FFT3D_FLAG_GENERIC | FFT3D_FLAG_EXPLICIT_TRANSPOSE |
-                         FFT3D_FLAG_FUSED_PLANE));
+                         FFT3D_FLAG_FUSED_PLANE | FFT3D_FLAG_PADDED_REAL));
 }
 
 // The cluster plane pass (rows + n1 columns of every plane, one cluster per plane).
@@ -477,6 +480,13 @@ std::string describe_plan(const fft3d_plan_s* p)
     return d;
 }
 
+// Bytes of the real side: n2 floats per row, or 2H in the padded layout.
+size_t real_bytes(const fft3d_plan_s* p)
+{
+    const size_t row = (p->flags & FFT3D_FLAG_PADDED_REAL) ? 2 * (size_t)p->H : (size_t)p->n2;
+    return (size_t)p->batch * p->n0 * p->n1 * row * sizeof(float);
+}
+
 bool overlaps(const void* a, size_t na, const void* b, size_t nb)
 {
     const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
@@ -509,8 +519,11 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
     if (n0 < 1 || n1 < 1 || n2 < 2 || batch < 1 || dtype < 0 || dtype > 2 ||
         (flags & ~(FFT3D_FLAG_EXPLICIT_TRANSPOSE | FFT3D_FLAG_TRANSPOSE_BACK | FFT3D_FLAG_THREE_PASS |
                    FFT3D_FLAG_GENERIC | FFT3D_FLAG_TEST_SKIP_ARRIVAL | FFT3D_FLAG_FUSED_PLANE |
-                   FFT3D_FLAG_CLUSTER_PLANE)) ||
-        ((flags & FFT3D_FLAG_TRANSPOSE_BACK) && !(flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE))) {
+                   FFT3D_FLAG_CLUSTER_PLANE | FFT3D_FLAG_PADDED_REAL | FFT3D_FLAG_PRESERVE_INPUT)) ||
+        ((flags & FFT3D_FLAG_TRANSPOSE_BACK) && !(flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE)) ||
+        // the padded layout and the input-preserving inverse run the transpose-free pass sequence
+        ((flags & (FFT3D_FLAG_PADDED_REAL | FFT3D_FLAG_PRESERVE_INPUT)) &&
+         (flags & (FFT3D_FLAG_EXPLICIT_TRANSPOSE | FFT3D_FLAG_FUSED_PLANE)))) {
         fail(FFT3D_ERR_INVALID_ARG);
         return nullptr;
     }
@@ -647,7 +660,8 @@ void fft3d_destroy(fft3d_handle p)
 size_t fft3d_workspace_bytes(fft3d_handle p)
 {
     if (!p) return 0;
-    if (p->flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE) return (size_t)p->batch * (size_t)p->M * sizeof(float2);
+    if (p->flags & (FFT3D_FLAG_EXPLICIT_TRANSPOSE | FFT3D_FLAG_PRESERVE_INPUT))
+        return (size_t)p->batch * (size_t)p->M * sizeof(float2);
     return 0;
 }
 
@@ -692,9 +706,10 @@ int fft3d_r2c(fft3d_handle p, const float* in, void* out, void* stream)
 {
     if (!p || !in || !out) return fail(FFT3D_ERR_INVALID_ARG);
     if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return fail(FFT3D_ERR_MISALIGNED);
-    const size_t in_bytes = (size_t)p->batch * p->N * sizeof(float);
+    const size_t in_bytes = real_bytes(p);
     const size_t out_bytes = (size_t)p->batch * p->M * sizeof(float2);
-    if (overlaps(in, in_bytes, out, out_bytes)) return fail(FFT3D_ERR_INVALID_ARG);
+    const bool in_place = (p->flags & FFT3D_FLAG_PADDED_REAL) && (const void*)in == out;
+    if (!in_place && overlaps(in, in_bytes, out, out_bytes)) return fail(FFT3D_ERR_INVALID_ARG);
     const bool xpose = p->flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE;
     if (xpose && !p->workspace) return fail(FFT3D_ERR_NO_WORKSPACE);
     cudaStream_t s = (cudaStream_t)stream;
@@ -740,13 +755,37 @@ int fft3d_c2r(fft3d_handle p, void* in, float* out, void* stream)
     if (!p || !in || !out) return fail(FFT3D_ERR_INVALID_ARG);
     if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return fail(FFT3D_ERR_MISALIGNED);
     const size_t in_bytes = (size_t)p->batch * p->M * sizeof(float2);
-    const size_t out_bytes = (size_t)p->batch * p->N * sizeof(float);
-    if (overlaps(in, in_bytes, out, out_bytes)) return fail(FFT3D_ERR_INVALID_ARG);
+    const size_t out_bytes = real_bytes(p);
+    const bool preserve = p->flags & FFT3D_FLAG_PRESERVE_INPUT;
+    const bool in_place = (p->flags & FFT3D_FLAG_PADDED_REAL) && in == (void*)out && !preserve;
+    if (!in_place && overlaps(in, in_bytes, out, out_bytes)) return fail(FFT3D_ERR_INVALID_ARG);
     const bool xpose = p->flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE;
-    if (xpose && !p->workspace) return fail(FFT3D_ERR_NO_WORKSPACE);
+    if ((xpose || preserve) && !p->workspace) return fail(FFT3D_ERR_NO_WORKSPACE);
     cudaStream_t s = (cudaStream_t)stream;
     const long long H = p->H, n0 = p->n0, n1 = p->n1, B = p->batch;
     float2* x = (float2*)in;
+    if (preserve && p->workspace && overlaps(in, in_bytes, p->workspace, in_bytes)) return fail(FFT3D_ERR_INVALID_ARG);
+    if (preserve) {
+        // the first column pass reads the input and writes the workspace; the
+        // rest runs there (the row c2r only reads its input)
+        float2* w = (float2*)p->workspace;
+        float2* src = x;
+        if (n0 > 1) {
+            if (run_col(p, p->ax0, +1, src, p->P, p->P, B, p->M, s, w) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+            src = w;
+        }
+        if (p->cplane) {
+            if (run_cplane(p, +1, src, out, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+            return FFT3D_OK;
+        }
+        if (n1 > 1) {
+            if (run_col(p, p->ax1, +1, src, H, H, B * n0, n1 * H, s, src == w ? nullptr : w) != cudaSuccess)
+                return fail(FFT3D_ERR_CUDA);
+            src = w;
+        }
+        if (run_row(p, +1, src, out, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        return FFT3D_OK;
+    }
     if (!xpose && p->cplane) {
         if (run_col(p, p->ax0, +1, x, p->P, p->P, B, p->M, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
         if (run_cplane(p, +1, x, out, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);

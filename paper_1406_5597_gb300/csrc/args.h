@@ -40,6 +40,7 @@ struct RowArgs {
     long long rows;
     const float2* tw;      // W_L^m, m in [0, L), L = n2/2
     const float2* twpack;  // exp(-2 pi i k / n2), k in [0, L]
+    long long rs;          // real-side row stride in float pairs: L (dense) or L + 1 (padded rows of 2H floats)
 };
 
 // Runtime radix plan for the generic (any 2/3/5-smooth length) kernels.

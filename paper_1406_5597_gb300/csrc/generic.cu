@@ -94,10 +94,10 @@ __global__ void generic_row_kernel(RowArgs a, GenPlan g, int G)
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthr = blockDim.x * blockDim.y;
     if (DIR < 0) {
-        const float2* in = reinterpret_cast<const float2*>(a.in) + row0 * L;
+        const float2* in = reinterpret_cast<const float2*>(a.in) + row0 * a.rs;
         for (int i = tid; i < L * G; i += nthr) {
             const int line = i / L, p = i % L;
-            b0[gi(p, line, G)] = line < nrows ? in[i] : make_float2(0.f, 0.f);
+            b0[gi(p, line, G)] = line < nrows ? in[line * a.rs + p] : make_float2(0.f, 0.f);
         }
         __syncthreads();
         float2* Z = generic_stages<-1>(g, b0, b1, G, a.tw);
@@ -144,10 +144,10 @@ __global__ void generic_row_kernel(RowArgs a, GenPlan g, int G)
         }
         __syncthreads();
         float2* z = generic_stages<+1>(g, b0, b1, G, a.tw);
-        float2* out = reinterpret_cast<float2*>(a.out) + row0 * L;
+        float2* out = reinterpret_cast<float2*>(a.out) + row0 * a.rs;
         for (int i = tid; i < L * nrows; i += nthr) {
             const int line = i / L, p = i % L;
-            out[i] = z[gi(p, line, G)];
+            out[line * a.rs + p] = z[gi(p, line, G)];
         }
     }
 }

@@ -80,12 +80,12 @@ __global__ void __launch_bounds__((L / E) * ROWS) row_r2c_kernel(RowArgs a)
     const int tid = r * T + t;
     const long long row0 = (long long)blockIdx.x * ROWS;
     const int nrows = (int)min((long long)ROWS, a.rows - row0);
-    const float2* in = reinterpret_cast<const float2*>(a.in) + row0 * L;  // packed z of each row
+    const float2* in = reinterpret_cast<const float2*>(a.in) + row0 * a.rs;  // packed z of each row
     float2* out = reinterpret_cast<float2*>(a.out) + row0 * H;
 
     for (int i = tid; i < ROWS * L; i += T * ROWS) {
         const int rr = i / L, p = i - rr * L;
-        sm[rr * RS + Ex::pad(p)] = (rr < nrows) ? in[i] : make_float2(0.f, 0.f);
+        sm[rr * RS + Ex::pad(p)] = (rr < nrows) ? in[rr * a.rs + p] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     Ex ex{sm + r * RS};
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__((L / E) * ROWS) row_c2r_kernel(RowArgs a)
     const long long row0 = (long long)blockIdx.x * ROWS;
     const int nrows = (int)min((long long)ROWS, a.rows - row0);
     const float2* in = reinterpret_cast<const float2*>(a.in) + row0 * H;
-    float2* out = reinterpret_cast<float2*>(a.out) + row0 * L;  // real row as float pairs
+    float2* out = reinterpret_cast<float2*>(a.out) + row0 * a.rs;  // real row as float pairs
 
     for (int i = tid; i < ROWS * H; i += T * ROWS) {
         const int rr = i / H, p = i - rr * H;
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__((L / E) * ROWS) row_c2r_kernel(RowArgs a)
     __syncthreads();
     for (int i = tid; i < nrows * L; i += T * ROWS) {
         const int rr = i / L, p = i - rr * L;
-        out[i] = sm[rr * RS + Ex::pad(p)];
+        out[rr * a.rs + p] = sm[rr * RS + Ex::pad(p)];
     }
 }
 
@@ -234,7 +234,7 @@ __device__ __forceinline__ void row_r2c_regs(float2 (&v)[E], float2* out_row, bo
 }
 
 // r2c of one row: in_row = packed row (L float2), out_row = H bins.
-template <int L, int E, bool CG>
+template <int L, int E, int CG>
 __device__ __forceinline__ void row_r2c_body(const float2* in_row, float2* out_row, bool active, int t, int lane,
                                              float2* sm_row, const float2* __restrict__ tw,
                                              const float2* __restrict__ twpack)
@@ -292,7 +292,7 @@ __device__ __forceinline__ void row_c2r_regs(const float2* in_row, bool active, 
 }
 
 // c2r of one row: in_row = H bins, out_row = packed real row (L float2).
-template <int L, int E, bool CG>
+template <int L, int E, int CG>
 __device__ __forceinline__ void row_c2r_body(const float2* in_row, float2* out_row, bool active, int t, int lane,
                                              float2* sm_row, const float2* __restrict__ tw,
                                              const float2* __restrict__ twpack)
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__((L / E) * ROWS) row_r2c_warp_kernel(RowArgs a)
     constexpr int H = L + 1;
     const int t = threadIdx.x, r = threadIdx.y;
     const long long row = (long long)blockIdx.x * blockDim.y + r;
-    row_r2c_body<L, E, false>(reinterpret_cast<const float2*>(a.in) + row * L,
+    row_r2c_body<L, E, kLdCg>(reinterpret_cast<const float2*>(a.in) + row * a.rs,
                               reinterpret_cast<float2*>(a.out) + row * H, row < a.rows, t, (r * T + t) & 31,
                               sm + r * RowLayout<L>::stride, a.tw, a.twpack);
 }
@@ -376,8 +376,8 @@ __global__ void __launch_bounds__((L / E) * ROWS) row_c2r_warp_kernel(RowArgs a)
     constexpr int H = L + 1;
     const int t = threadIdx.x, r = threadIdx.y;
     const long long row = (long long)blockIdx.x * blockDim.y + r;
-    row_c2r_body<L, E, false>(reinterpret_cast<const float2*>(a.in) + row * H,
-                              reinterpret_cast<float2*>(a.out) + row * L, row < a.rows, t, (r * T + t) & 31,
+    row_c2r_body<L, E, kLdCg>(reinterpret_cast<const float2*>(a.in) + row * H,
+                              reinterpret_cast<float2*>(a.out) + row * a.rs, row < a.rows, t, (r * T + t) & 31,
                               sm + r * RowLayout<L>::stride, a.tw, a.twpack);
 }
 

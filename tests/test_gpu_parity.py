@@ -260,6 +260,102 @@ def test_plane_form_every_cluster_size_and_autotune(cuda_lib, shape):
     assert lib.fft3d_set_plane_choice(tp.handle, sizes[-1]) == lib.FFT3D_ERR_INVALID_ARG
 
 
+PADDED_SHAPES = [(32, 32, 32), (64, 64, 64), (6, 512, 60), (8, 6, 1024), (3, 2, 2048), (2, 3, 4096), (48, 80, 96),
+                 (5, 3, 2), (1, 8, 16)]
+
+
+@pytest.mark.parametrize("extra", ["plain", "generic", "tc"])
+@pytest.mark.parametrize("shape", PADDED_SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_padded_real_layout_in_and_out_of_place(cuda_lib, shape, extra):
+    """FFTW's padded real layout (rows of 2H floats): r2c and c2r out of place
+    and in place match the oracle; r2c never reads the padding (NaN there) and
+    an out-of-place c2r never writes it."""
+    lib = cuda_lib
+    n0, n1, n2 = shape
+    H = n2 // 2 + 1
+    flags = lib.FFT3D_FLAG_PADDED_REAL | (lib.FFT3D_FLAG_GENERIC if extra == "generic" else 0)
+    dtype = lib.FFT3D_F32_TC_BF16X3 if extra == "tc" else lib.FFT3D_F32
+    tol = 1e-5 if extra == "tc" else TOL
+    try:
+        plan = lib.Plan(n0, n1, n2, dtype=dtype, flags=flags)
+    except lib.Fft3dError as e:
+        assert extra == "tc" and e.status == lib.FFT3D_ERR_UNSUPPORTED_SIZE  # no tensor-core axis at this size
+        return
+    s = torch.cuda.current_stream().cuda_stream
+    x32 = synth.uniform_field(shape, seed=71).astype(np.float32)
+    Xo = oracle.r2c3d(x32.astype(np.float64))
+    xp = np.full((n0, n1, 2 * H), np.nan, dtype=np.float32)
+    xp[..., :n2] = x32
+    buf = torch.from_numpy(xp).cuda()
+    X = torch.empty((n0, n1, H), dtype=torch.complex64, device="cuda")
+    plan.r2c(buf.data_ptr(), X.data_ptr(), s)
+    torch.cuda.synchronize()
+    assert rel_l2(X.cpu().numpy(), Xo) <= tol
+    plan.r2c(buf.data_ptr(), buf.data_ptr(), s)  # in place
+    torch.cuda.synchronize()
+    assert rel_l2(buf.view(torch.complex64).cpu().numpy(), Xo) <= tol
+    Y = random_half_spectrum((n0, n1, H), seed=72)
+    yo = oracle.c2r3d(Y.astype(np.complex128), n2)
+    Yd = torch.from_numpy(Y).cuda()
+    out = torch.full((n0, n1, 2 * H), 7.0, dtype=torch.float32, device="cuda")
+    plan.c2r(Yd.data_ptr(), out.data_ptr(), s)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    assert rel_l2(o[..., :n2], yo) <= tol
+    assert np.all(o[..., n2:] == 7.0)
+    Yd = torch.from_numpy(Y).cuda()
+    plan.c2r(Yd.data_ptr(), Yd.data_ptr(), s)  # in place
+    torch.cuda.synchronize()
+    assert rel_l2(Yd.view(torch.float32).cpu().numpy().reshape(n0, n1, 2 * H)[..., :n2], yo) <= tol
+    # a partial overlap is still rejected
+    assert lib.fft3d_r2c(plan.handle, buf.data_ptr(), buf.data_ptr() + 16, s) == lib.FFT3D_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("shape,plane", [((32, 32, 32), 0), ((5, 128, 128), 2), ((1, 8, 16), 0), ((4, 1, 8), 0),
+                                         ((6, 512, 60), 0), ((64, 64, 64), 1)],
+                         ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else f"plane{v}")
+def test_preserve_input_c2r(cuda_lib, shape, plane):
+    """FFT3D_FLAG_PRESERVE_INPUT: c2r leaves its input bit for bit unchanged
+    (the first column pass writes the plan's workspace) and still matches the
+    oracle, with the separate passes or a cluster plane kernel."""
+    lib = cuda_lib
+    n0, n1, n2 = shape
+    H = n2 // 2 + 1
+    for flags in (lib.FFT3D_FLAG_PRESERVE_INPUT, lib.FFT3D_FLAG_PRESERVE_INPUT | lib.FFT3D_FLAG_PADDED_REAL):
+        plan = lib.Plan(n0, n1, n2, flags=flags)
+        assert lib.fft3d_workspace_bytes(plan.handle) == n0 * n1 * H * 8
+        if plane and not flags & lib.FFT3D_FLAG_PADDED_REAL:
+            assert lib.fft3d_set_plane_choice(plan.handle, plane) == lib.FFT3D_OK
+        s = torch.cuda.current_stream().cuda_stream
+        Y = random_half_spectrum((n0, n1, H), seed=73)
+        yo = oracle.c2r3d(Y.astype(np.complex128), n2)
+        Yd = torch.from_numpy(Y).cuda()
+        keep = Yd.clone()
+        rw = 2 * H if flags & lib.FFT3D_FLAG_PADDED_REAL else n2
+        out = torch.empty((n0, n1, rw), dtype=torch.float32, device="cuda")
+        plan.c2r(Yd.data_ptr(), out.data_ptr(), s)
+        torch.cuda.synchronize()
+        assert torch.equal(Yd, keep)
+        assert rel_l2(out.cpu().numpy()[..., :n2], yo) <= TOL
+        assert lib.fft3d_c2r(plan.handle, Yd.data_ptr(), Yd.data_ptr(), s) == lib.FFT3D_ERR_INVALID_ARG
+
+
+def test_padded_and_preserve_flag_combinations(cuda_lib):
+    lib = cuda_lib
+    for bad in (lib.FFT3D_FLAG_PADDED_REAL | lib.FFT3D_FLAG_EXPLICIT_TRANSPOSE,
+                lib.FFT3D_FLAG_PRESERVE_INPUT | lib.FFT3D_FLAG_FUSED_PLANE):
+        assert not lib.fft3d_plan_variant(32, 32, 32, lib.FFT3D_F32, 1, bad)
+        assert lib.fft3d_last_error() == lib.FFT3D_ERR_INVALID_ARG
+    plan = lib.Plan(32, 32, 32, flags=lib.FFT3D_FLAG_PADDED_REAL)
+    assert lib.fft3d_set_plane_choice(plan.handle, 2) == lib.FFT3D_ERR_INVALID_ARG
+    raw = lib.fft3d_plan_variant(32, 32, 32, lib.FFT3D_F32, 1, lib.FFT3D_FLAG_PRESERVE_INPUT)
+    x = torch.empty(32 * 32 * 17, dtype=torch.complex64, device="cuda")
+    y = torch.empty(32 ** 3, dtype=torch.float32, device="cuda")
+    assert lib.fft3d_c2r(raw, x.data_ptr(), y.data_ptr(), torch.cuda.current_stream().cuda_stream) == \
+        lib.FFT3D_ERR_NO_WORKSPACE
+    lib.fft3d_destroy(raw)
+
+
 def test_bounded_wait_gives_up_without_hanging(cuda_lib):
     """Failure detection without a GPU fault: with the test hook, the
     producers of plane 0 never report, so the consumers' bounded waits give up
