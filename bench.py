@@ -448,6 +448,33 @@ def main():
         nl.close()
         del U, out
 
+    # one Heun step of the pseudo-spectral Navier-Stokes equations at 256^3
+    # (nonlinear term twice + two fused stage kernels), replayed as one graph
+    if not args.no_variants:
+        m = 256
+        ns = fft3d.NavierStokes(m, m, m)
+        import synth
+        U = torch.from_numpy(synth.spectral_velocity(m, m, m, seed=synth.seed_for_config(4)).astype(np.complex64)).to(dev)
+        Mc = m * m * (m // 2 + 1)
+        nss = torch.cuda.Stream(dev)
+        nss.wait_stream(stream)
+        with torch.cuda.stream(nss):
+            for _ in range(3):
+                ns.step(U, 0.01, 1e-3, stream=nss)
+            reps = 20
+            sms = time_steps(lambda: ns.step(U, 0.01, 1e-3, stream=nss), nss, reps) / reps
+        # two nonlinear terms as run, and the two stage passes: u (3 fields) in,
+        # the six products read only inside the 2/3 rule (fraction f of the bins),
+        # u* and the accumulator out (stage 1); u*, products, accumulator in, u out (stage 2)
+        kept = (2 * ((m - 1) // 3) + 1) ** 2 * ((m - 1) // 3 + 1)
+        f = kept / Mc
+        run_bytes = int(2 * 360 * Mc + 8 * Mc * ((3 + 6 * f + 6) + (3 + 6 * f + 3 + 3)))
+        line["navier_stokes_256"] = {"ms_per_step": sms, "gbs_passes_run": run_bytes / (sms * 1e-3) / 1e9,
+                                     "passes_run_bytes": run_bytes, "launches": fft3d.fft3d_ns_launches(ns.handle),
+                                     "graph": True, "scheme": "Heun RK2, nu = 0.01, dt = 1e-3"}
+        ns.close()
+        del U
+
     # grouped uneven batch: 64^3, 96^3, 128^3, 192^3, 160^3 x 4 fields, r2c + c2r,
     # each direction one graph launch, shapes autotuned
     if not args.no_variants:

@@ -283,6 +283,45 @@ int fft3d_nonlinear_launches(fft3d_nl_handle nl);
 void fft3d_nonlinear_destroy(fft3d_nl_handle nl);
 
 /*
+ * One time step of the incompressible Navier-Stokes equations in a periodic
+ * box [0, 2 pi)^3, pseudo-spectral (the Tarang-type solver of Sec. 1; the
+ * paper names the method, the scheme below is this library's): the velocity is
+ * held as three half spectra uhat_i (u_i = c2r(uhat_i)), and
+ *     R_l(uhat) = mask * (-i P_lm(k) sum_j k_j N_mj - nu |k|^2 uhat_l),
+ * N = the dealiased quadratic term of fft3d_nonlinear_exec, P = I - k k^T/|k|^2
+ * (the pressure projection; zero at k = 0), mask = the 2/3 rule (bins outside
+ * it never change).  Heun's two-stage method:
+ *     u* = u + dt R(u),   u <- u + dt/2 (R(u) + R(u*)).
+ * Per step: the nonlinear term twice (5 launches each) and two fused
+ * elementwise stage kernels (divergence, projection, viscous term, update);
+ * on a non-default stream the 12 launches are captured once into a CUDA graph
+ * per (uhat, workspace, nu, dt) and replayed; on the legacy default stream they
+ * are launched directly.  FP32 storage and arithmetic.  Supported shapes: as
+ * fft3d_nonlinear_plan (else UNSUPPORTED_SIZE).
+ */
+typedef struct fft3d_ns_s* fft3d_ns_handle;
+
+/* Plan for n0 x n1 x n2 fields (blocks; NULL on error, see fft3d_last_error). */
+fft3d_ns_handle fft3d_ns_plan(int n0, int n1, int n2);
+
+/* Caller workspace: 15 * n0 * n1 * (n2/2+1) complex64 values (u*, the Heun
+ * accumulator, the six product spectra, the nonlinear term's scratch);
+ * 256-byte aligned. */
+size_t fft3d_ns_workspace_bytes(fft3d_ns_handle ns);
+int fft3d_ns_set_workspace(fft3d_ns_handle ns, void* dev_ptr);
+
+/* uhat: 3 contiguous half spectra (device), advanced in place by one step of
+ * size dt with kinematic viscosity nu (nu >= 0, dt > 0); 16-byte aligned; must
+ * not overlap the workspace. */
+int fft3d_ns_step(fft3d_ns_handle ns, void* uhat, float nu, float dt, void* stream);
+
+/* Kernel launches per fft3d_ns_step. */
+int fft3d_ns_launches(fft3d_ns_handle ns);
+
+/* NULL-safe; blocks on the device. */
+void fft3d_ns_destroy(fft3d_ns_handle ns);
+
+/*
  * FP64 spectral diagnostics of a half spectrum (device-side checks of a
  * transform, and the energy spectrum of a pseudo-spectral solver, Sec. 1).
  * spec:   batch*n0*n1*H float2 (device), read only, laid out as fft3d_r2c

@@ -248,3 +248,52 @@ def nonlinear_term(uhat: np.ndarray, n2: int) -> np.ndarray:
     for q, (i, j) in enumerate(((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))):
         out[q] = np.where(mask, r2c3d(u[i] * u[j]) / N, 0.0)
     return out
+
+
+def wavenumbers(n0: int, n1: int, n2: int):
+    """Signed integer wavenumbers of the half-spectrum bins (box [0, 2 pi)^3):
+    k_a = j_a for j_a < n_a/2, j_a - n_a otherwise (the Nyquist index maps to
+    -n_a/2); k2 = j2.  Broadcastable (n0,1,1), (1,n1,1), (1,1,H) arrays."""
+    H = n2 // 2 + 1
+
+    def signed(n):
+        j = np.arange(n)
+        return np.where(j < n // 2, j, j - n).astype(np.float64)
+
+    return signed(n0)[:, None, None], signed(n1)[None, :, None], np.arange(H, dtype=np.float64)[None, None, :]
+
+
+def ns_rhs(uhat: np.ndarray, n2: int, nu: float) -> np.ndarray:
+    """Right-hand side of the incompressible Navier-Stokes equations in
+    Fourier space for the velocity half-spectra uhat (3, n0, n1, n2/2+1) with
+    u = c2r(uhat) (the pseudo-spectral solver of Sec. 1; the scheme itself is
+    not printed in the paper):
+        a_l = sum_j k_j N_lj                (N = nonlinear_term: the dealiased
+                                             Fourier coefficients of u_l u_j)
+        b   = a - k (k . a) / |k|^2         (pressure projection; b = 0 at k = 0)
+        R_l = mask * (-i b_l - nu |k|^2 uhat_l),
+    i.e. the transform of -(u . grad) u - grad p + nu lap u for a solenoidal u."""
+    uhat = np.asarray(uhat, dtype=np.complex128)
+    _, n0, n1, H = uhat.shape
+    N = nonlinear_term(uhat, n2)
+    k = wavenumbers(n0, n1, n2)
+    sym = {(0, 0): 0, (0, 1): 1, (0, 2): 2, (1, 1): 3, (1, 2): 4, (2, 2): 5}
+    a = [sum(k[j] * N[sym[(min(l, j), max(l, j))]] for j in range(3)) for l in range(3)]
+    kk = k[0] ** 2 + k[1] ** 2 + k[2] ** 2
+    ka = k[0] * a[0] + k[1] * a[1] + k[2] * a[2]
+    inv = np.divide(1.0, kk, out=np.zeros_like(kk), where=kk > 0)
+    mask = dealias_mask(n0, n1, n2)
+    R = np.empty_like(uhat)
+    for l in range(3):
+        b = np.where(kk > 0, a[l] - k[l] * ka * inv, 0.0)
+        R[l] = np.where(mask, -1j * b - nu * kk * uhat[l], 0.0)
+    return R
+
+
+def ns_step_rk2(uhat: np.ndarray, n2: int, nu: float, dt: float) -> np.ndarray:
+    """One step of Heun's two-stage Runge-Kutta method on ns_rhs:
+        u* = u + dt R(u);  u_new = u + dt/2 (R(u) + R(u*))."""
+    uhat = np.asarray(uhat, dtype=np.complex128)
+    r1 = ns_rhs(uhat, n2, nu)
+    r2 = ns_rhs(uhat + dt * r1, n2, nu)
+    return uhat + 0.5 * dt * (r1 + r2)

@@ -73,6 +73,12 @@ _SIGS = {
     "fft3d_nonlinear_exec": ([_P, _P, _P, _P], _I),
     "fft3d_nonlinear_launches": ([_P], _I),
     "fft3d_nonlinear_destroy": ([_P], None),
+    "fft3d_ns_plan": ([_I, _I, _I], _P),
+    "fft3d_ns_workspace_bytes": ([_P], ctypes.c_size_t),
+    "fft3d_ns_set_workspace": ([_P, _P], _I),
+    "fft3d_ns_step": ([_P, _P, ctypes.c_float, ctypes.c_float, _P], _I),
+    "fft3d_ns_launches": ([_P], _I),
+    "fft3d_ns_destroy": ([_P], None),
     "fft3d_autotune": ([_P, _P, _P, _I, _P], _I),
     "fft3d_get_choices": ([_P, _P], _I),
     "fft3d_set_choices": ([_P, _P], _I),
@@ -305,6 +311,69 @@ def fft3d_set_choices(plan, choices):
         raise ValueError("five choices: w0, w1, rows, tma0, tma1")
     c = (ctypes.c_int * 5)(*choices)
     return load().fft3d_set_choices(_v(plan), c)
+
+
+def fft3d_ns_plan(n0, n1, n2):
+    return load().fft3d_ns_plan(n0, n1, n2)
+
+
+def fft3d_ns_workspace_bytes(ns):
+    return load().fft3d_ns_workspace_bytes(_v(ns))
+
+
+def fft3d_ns_set_workspace(ns, dev_ptr):
+    return load().fft3d_ns_set_workspace(_v(ns), _v(dev_ptr))
+
+
+def fft3d_ns_step(ns, uhat_ptr, nu, dt, stream=0):
+    return load().fft3d_ns_step(_v(ns), _v(uhat_ptr), float(nu), float(dt), _v(stream))
+
+
+def fft3d_ns_launches(ns):
+    return load().fft3d_ns_launches(_v(ns))
+
+
+def fft3d_ns_destroy(ns):
+    load().fft3d_ns_destroy(_v(ns))
+
+
+class NavierStokes:
+    """Owning wrapper of fft3d_ns_*: workspace from torch, then
+    step(uhat, nu, dt) advances the (3, n0, n1, n2/2+1) complex64 CUDA tensor
+    uhat in place by one Heun step."""
+
+    def __init__(self, n0, n1, n2):
+        import torch
+        h = fft3d_ns_plan(n0, n1, n2)
+        if not h:
+            raise Fft3dError(fft3d_last_error(), "fft3d_ns_plan")
+        self.handle = h
+        self.shape = (n0, n1, n2)
+        self._ws = torch.empty(fft3d_ns_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+        st = fft3d_ns_set_workspace(h, self._ws.data_ptr())
+        if st != FFT3D_OK:
+            raise Fft3dError(st, "fft3d_ns_set_workspace")
+
+    def step(self, uhat, nu, dt, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        s = stream.cuda_stream if stream is not False else 0
+        st = fft3d_ns_step(self.handle, uhat.data_ptr(), nu, dt, s)
+        if st != FFT3D_OK:
+            raise Fft3dError(st, "fft3d_ns_step")
+        return uhat
+
+    def close(self):
+        if self.handle:
+            fft3d_ns_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fft3d_get_plane_choice(plan):

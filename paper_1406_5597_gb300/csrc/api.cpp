@@ -24,6 +24,7 @@
 #include "energy.h"
 #include "fft3d.h"
 #include "cplane.h"
+#include "ns.h"
 #include "plane.h"
 #include "tma_host.h"
 
@@ -968,6 +969,121 @@ int fft3d_nonlinear_exec(fft3d_nl_handle nl, const void* uhat, void* nhat, void*
         nl->g_ws = nl->workspace;
     }
     return cudaGraphLaunch(nl->exec, s) == cudaSuccess ? FFT3D_OK : fail(FFT3D_ERR_CUDA);
+}
+
+// ---------------------------------------------------------------------------
+// Pseudo-spectral Navier-Stokes step (Heun) around the nonlinear term.
+// ---------------------------------------------------------------------------
+struct fft3d_ns_s {
+    fft3d_nl_s* nl = nullptr;      // the nonlinear term (and its batch-1 plan)
+    void* workspace = nullptr;     // [u* 3M][acc 3M][nhat 6M][nonlinear scratch 3M]
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void* g_u = nullptr;     // operands the graph was captured with
+    void* g_ws = nullptr;
+    float g_nu = 0.f, g_dt = 0.f;
+};
+
+namespace {
+
+void drop_ns_graph(fft3d_ns_s* ns)
+{
+    if (ns->exec) cudaGraphExecDestroy(ns->exec);
+    if (ns->graph) cudaGraphDestroy(ns->graph);
+    ns->exec = nullptr;
+    ns->graph = nullptr;
+    ns->g_u = nullptr;
+    ns->g_ws = nullptr;
+}
+
+cudaError_t enqueue_ns_step(fft3d_ns_s* ns, float2* u, float nu, float dt, cudaStream_t s)
+{
+    const fft3d_plan_s* p = ns->nl->plan;
+    const long long M = p->M;
+    float2* w = (float2*)ns->workspace;
+    NsArgs a{u, w, w + 3 * M, w + 6 * M, p->n0, p->n1, p->n2, (int)p->H, M, nu, dt};
+    cudaError_t e;
+    if ((e = enqueue_nonlinear(ns->nl, u, w + 6 * M, s)) != cudaSuccess) return e;
+    if ((e = launch_ns_stage(a, 1, s)) != cudaSuccess) return e;
+    if ((e = enqueue_nonlinear(ns->nl, w, w + 6 * M, s)) != cudaSuccess) return e;
+    return launch_ns_stage(a, 2, s);
+}
+
+}  // namespace
+
+fft3d_ns_handle fft3d_ns_plan(int n0, int n1, int n2)
+{
+    fft3d_nl_handle nl = fft3d_nonlinear_plan(n0, n1, n2);
+    if (!nl) return nullptr;
+    fft3d_ns_s* ns = new (std::nothrow) fft3d_ns_s();
+    if (!ns) {
+        fft3d_nonlinear_destroy(nl);
+        fail(FFT3D_ERR_ALLOC);
+        return nullptr;
+    }
+    ns->nl = nl;
+    return ns;
+}
+
+size_t fft3d_ns_workspace_bytes(fft3d_ns_handle ns)
+{
+    return ns ? (size_t)15 * (size_t)ns->nl->plan->M * sizeof(float2) : 0;
+}
+
+int fft3d_ns_set_workspace(fft3d_ns_handle ns, void* dev_ptr)
+{
+    if (!ns) return fail(FFT3D_ERR_INVALID_ARG);
+    if (dev_ptr && ((uintptr_t)dev_ptr & 255)) return fail(FFT3D_ERR_MISALIGNED);
+    ns->workspace = dev_ptr;
+    ns->nl->workspace = dev_ptr ? (char*)dev_ptr + (size_t)12 * ns->nl->plan->M * sizeof(float2) : nullptr;
+    return FFT3D_OK;
+}
+
+int fft3d_ns_step(fft3d_ns_handle ns, void* uhat, float nu, float dt, void* stream)
+{
+    if (!ns || !uhat || !(nu >= 0.f) || !(dt > 0.f)) return fail(FFT3D_ERR_INVALID_ARG);
+    if (!ns->workspace) return fail(FFT3D_ERR_NO_WORKSPACE);
+    if ((uintptr_t)uhat & 15) return fail(FFT3D_ERR_MISALIGNED);
+    const size_t M8 = (size_t)ns->nl->plan->M * sizeof(float2);
+    if (overlaps(uhat, 3 * M8, ns->workspace, 15 * M8)) return fail(FFT3D_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    float2* u = (float2*)uhat;
+    if (!s) return enqueue_ns_step(ns, u, nu, dt, s) == cudaSuccess ? FFT3D_OK : fail(FFT3D_ERR_CUDA);
+    if (!(ns->exec && ns->g_u == uhat && ns->g_ws == ns->workspace && ns->g_nu == nu && ns->g_dt == dt)) {
+        drop_ns_graph(ns);
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+        const cudaError_t e = enqueue_ns_step(ns, u, nu, dt, s);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            return fail(FFT3D_ERR_CUDA);
+        }
+        ns->graph = g;
+        if (cudaGraphInstantiate(&ns->exec, g, 0) != cudaSuccess) {
+            drop_ns_graph(ns);
+            return fail(FFT3D_ERR_CUDA);
+        }
+        ns->g_u = uhat;
+        ns->g_ws = ns->workspace;
+        ns->g_nu = nu;
+        ns->g_dt = dt;
+    }
+    return cudaGraphLaunch(ns->exec, s) == cudaSuccess ? FFT3D_OK : fail(FFT3D_ERR_CUDA);
+}
+
+int fft3d_ns_launches(fft3d_ns_handle ns)
+{
+    return ns ? 2 * 5 + 2 : fail(FFT3D_ERR_INVALID_ARG);
+}
+
+void fft3d_ns_destroy(fft3d_ns_handle ns)
+{
+    if (!ns) return;
+    cudaDeviceSynchronize();
+    drop_ns_graph(ns);
+    fft3d_nonlinear_destroy(ns->nl);
+    delete ns;
 }
 
 int fft3d_nonlinear_launches(fft3d_nl_handle nl)

@@ -68,6 +68,10 @@ def test_null_handles(lib):
     assert fft3d.fft3d_launches_per_call(None) == fft3d.FFT3D_ERR_INVALID_ARG
     fft3d.fft3d_destroy(None)
     assert fft3d.fft3d_set_plane_choice(None, 2) == fft3d.FFT3D_ERR_INVALID_ARG
+    assert fft3d.fft3d_ns_step(None, 16, 0.01, 0.1) == fft3d.FFT3D_ERR_INVALID_ARG
+    assert fft3d.fft3d_ns_workspace_bytes(None) == 0
+    assert fft3d.fft3d_ns_launches(None) == fft3d.FFT3D_ERR_INVALID_ARG
+    fft3d.fft3d_ns_destroy(None)
     with pytest.raises(fft3d.Fft3dError):
         fft3d.fft3d_get_plane_choice(None)
     buf = ctypes.create_string_buffer(8)

@@ -280,3 +280,78 @@ def test_dealias_mask_counts():
     keep2 = (10 - 1) // 3 + 1
     assert m.sum() == keep0 * keep1 * keep2
     assert not m[12].any() and not m[:, 6].any()
+
+
+# ---------------------------------------------------------------------------
+# Pseudo-spectral Navier-Stokes step (ns_rhs, ns_step_rk2)
+# ---------------------------------------------------------------------------
+
+def _grid(n0, n1, n2):
+    x0 = 2 * np.pi * np.arange(n0)[:, None, None] / n0
+    x1 = 2 * np.pi * np.arange(n1)[None, :, None] / n1
+    x2 = 2 * np.pi * np.arange(n2)[None, None, :] / n2
+    return x0, x1, x2
+
+
+def _uhat_of(u, n2):
+    """Fourier coefficients (u = c2r(uhat)) of a sampled real field."""
+    n0, n1 = u.shape[:2]
+    return oracle.r2c3d(u) / (n0 * n1 * n2)
+
+
+def test_ns_shear_mode_decays_by_the_exact_rk2_factor():
+    """u = (sin(m x1), 0, 0) has (u . grad) u = 0, so R = -nu m^2 uhat and one
+    Heun step multiplies the field by 1 - z + z^2/2, z = nu m^2 dt."""
+    n0, n1, n2 = 8, 12, 16
+    m, nu, dt = 2, 0.05, 0.3
+    x0, x1, x2 = _grid(n0, n1, n2)
+    u = np.zeros((3, n0, n1, n2))
+    u[0] = np.sin(m * x1) + 0 * x0 + 0 * x2
+    uh = np.stack([_uhat_of(u[i], n2) for i in range(3)])
+    z = nu * m * m * dt
+    new = oracle.ns_step_rk2(uh, n2, nu, dt)
+    assert np.allclose(new, uh * (1 - z + z * z / 2), atol=1e-14)
+    assert np.allclose(oracle.ns_rhs(uh, n2, nu), -nu * m * m * uh, atol=1e-14)
+
+
+def test_ns_two_mode_triad_closed_form():
+    """u = (A cos x1, 0, B cos x0) is solenoidal with (u . grad) u =
+    (0, 0, -A B cos x1 sin x0), itself solenoidal (no pressure), so
+    du/dt = (0, 0, A B sin x0 cos x1) - nu u."""
+    n0, n1, n2 = 12, 12, 12
+    A, B, nu = 0.7, -1.3, 0.02
+    x0, x1, x2 = _grid(n0, n1, n2)
+    u = np.zeros((3, n0, n1, n2))
+    u[0] = A * np.cos(x1) + 0 * x0 + 0 * x2
+    u[2] = B * np.cos(x0) + 0 * x1 + 0 * x2
+    uh = np.stack([_uhat_of(u[i], n2) for i in range(3)])
+    dudt = np.zeros_like(u)
+    dudt[0] = -nu * u[0]
+    dudt[2] = A * B * np.sin(x0) * np.cos(x1) - nu * u[2]
+    expect = np.stack([_uhat_of(dudt[i], n2) for i in range(3)])
+    R = oracle.ns_rhs(uh, n2, nu)
+    assert np.max(np.abs(R - expect)) <= 1e-14
+    # a sign or axis slip would put the source term elsewhere: it is nonzero
+    assert np.max(np.abs(expect[2])) > 0.1
+
+
+def test_ns_rhs_conserves_energy_without_viscosity_and_is_solenoidal():
+    """For a solenoidal field inside the 2/3 mask the dealiased nonlinear
+    term exchanges energy between modes without creating any:
+    sum_half c_k2 Re(conj(uhat) . R) = 0 at nu = 0; with nu > 0 the rate is
+    -nu sum c_k2 |k|^2 |uhat|^2; and k . R = 0 everywhere."""
+    n0, n1, n2 = 16, 16, 16
+    uh = synth.spectral_velocity(n0, n1, n2, seed=91).astype(np.complex128)
+    w = oracle.half_weights(n2)
+    k = oracle.wavenumbers(n0, n1, n2)
+    kk = k[0] ** 2 + k[1] ** 2 + k[2] ** 2
+    R0 = oracle.ns_rhs(uh, n2, 0.0)
+    scale = np.sqrt(np.sum(np.abs(uh) ** 2) * np.sum(np.abs(R0) ** 2))
+    rate = np.sum(w * np.real(np.conj(uh) * R0))
+    assert abs(rate) <= 1e-12 * scale
+    assert np.max(np.abs(sum(k[i] * R0[i] for i in range(3)))) <= 1e-12 * np.max(np.abs(R0))
+    nu = 0.01
+    R = oracle.ns_rhs(uh, n2, nu)
+    rate = np.sum(w * np.real(np.conj(uh) * R))
+    expect = -nu * np.sum(w * kk * np.abs(uh) ** 2)
+    assert abs(rate - expect) <= 1e-12 * scale
