@@ -63,10 +63,10 @@ int fail(int status)
     return status;
 }
 
-bool smooth235(long long n)
+bool smooth2357(long long n)
 {
     if (n < 1) return false;
-    for (int p : {2, 3, 5})
+    for (int p : {2, 3, 5, 7})
         while (n % p == 0) n /= p;
     return n == 1;
 }
@@ -119,7 +119,7 @@ GenPlan generic_radices(int L)
     int rem = L;
     while (rem > 1) {
         int R = 0;
-        for (int cand : {8, 4, 2, 3, 5})
+        for (int cand : {8, 4, 2, 3, 5, 7})
             if (rem % cand == 0) { R = cand; break; }
         g.radix[g.nst++] = R;
         rem /= R;
@@ -503,7 +503,7 @@ const char* fft3d_error_string(int status)
     switch (status) {
     case FFT3D_OK: return "ok";
     case FFT3D_ERR_INVALID_ARG: return "invalid argument";
-    case FFT3D_ERR_UNSUPPORTED_SIZE: return "unsupported size (n2 must be even; n0, n1, n2/2 must be 2,3,5-smooth and <= 4096)";
+    case FFT3D_ERR_UNSUPPORTED_SIZE: return "unsupported size (n2 must be even; n0, n1, n2/2 must be 2,3,5,7-smooth and <= 4096)";
     case FFT3D_ERR_MISALIGNED: return "data pointer not 16-byte aligned";
     case FFT3D_ERR_ALLOC: return "device allocation failed";
     case FFT3D_ERR_CUDA: return "CUDA error";
@@ -528,7 +528,7 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
         fail(FFT3D_ERR_INVALID_ARG);
         return nullptr;
     }
-    if ((n2 & 1) || !smooth235(n0) || !smooth235(n1) || !smooth235(n2 / 2) || n0 > kMaxAxis || n1 > kMaxAxis ||
+    if ((n2 & 1) || !smooth2357(n0) || !smooth2357(n1) || !smooth2357(n2 / 2) || n0 > kMaxAxis || n1 > kMaxAxis ||
         n2 / 2 > kMaxAxis) {
         fail(FFT3D_ERR_UNSUPPORTED_SIZE);
         return nullptr;

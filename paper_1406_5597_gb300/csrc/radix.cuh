@@ -1,4 +1,4 @@
-// Register-resident small DFT codelets (radix 2, 3, 4, 5, 8, 16, 32) in FP32.
+// Register-resident small DFT codelets (radix 2, 3, 4, 5, 7, 8, 16, 32) in FP32.
 //
 // DIR = -1 is the forward kernel exp(-2 pi i / R), DIR = +1 the inverse.
 // Every codelet maps a[0..R-1] (natural order) to its DFT (natural order),
@@ -146,6 +146,37 @@ struct Dft<5, DIR> {
     }
 };
 
+// 7 points: with t_j = a_j + a_{7-j}, d_j = a_j - a_{7-j} (j = 1, 2, 3),
+//   X[m]   = a_0 + sum_j cos(2 pi j m / 7) t_j + DIR i sum_j sin(2 pi j m / 7) d_j,
+//   X[7-m] = the same with the sine sum negated  (m = 1, 2, 3).
+template <int DIR>
+struct Dft<7, DIR> {
+    __device__ __forceinline__ static void run(float2* a)
+    {
+        constexpr float c1 = 0.62348980185873353053f, c2 = -0.22252093395631440429f, c3 = -0.90096886790241912624f;
+        constexpr float s1 = 0.78183148246802980871f, s2 = 0.97492791218182360702f, s3 = 0.43388373911755812048f;
+        const float2 a0 = a[0];
+        const float2 t1 = cadd(a[1], a[6]), d1 = csub(a[1], a[6]);
+        const float2 t2 = cadd(a[2], a[5]), d2 = csub(a[2], a[5]);
+        const float2 t3 = cadd(a[3], a[4]), d3 = csub(a[3], a[4]);
+        // cos / sin of 2 pi (j m mod 7) / 7 for m = 1, 2, 3 and j = 1, 2, 3
+        const float2 r1 = make_float2(a0.x + c1 * t1.x + c2 * t2.x + c3 * t3.x, a0.y + c1 * t1.y + c2 * t2.y + c3 * t3.y);
+        const float2 r2 = make_float2(a0.x + c2 * t1.x + c3 * t2.x + c1 * t3.x, a0.y + c2 * t1.y + c3 * t2.y + c1 * t3.y);
+        const float2 r3 = make_float2(a0.x + c3 * t1.x + c1 * t2.x + c2 * t3.x, a0.y + c3 * t1.y + c1 * t2.y + c2 * t3.y);
+        const float2 q1 = make_float2(s1 * d1.x + s2 * d2.x + s3 * d3.x, s1 * d1.y + s2 * d2.y + s3 * d3.y);
+        const float2 q2 = make_float2(s2 * d1.x - s3 * d2.x - s1 * d3.x, s2 * d1.y - s3 * d2.y - s1 * d3.y);
+        const float2 q3 = make_float2(s3 * d1.x - s1 * d2.x + s2 * d3.x, s3 * d1.y - s1 * d2.y + s2 * d3.y);
+        const float2 i1 = mul_i<DIR>(q1), i2 = mul_i<DIR>(q2), i3 = mul_i<DIR>(q3);
+        a[0] = cadd(a0, cadd(t1, cadd(t2, t3)));
+        a[1] = cadd(r1, i1);
+        a[6] = csub(r1, i1);
+        a[2] = cadd(r2, i2);
+        a[5] = csub(r2, i2);
+        a[3] = cadd(r3, i3);
+        a[4] = csub(r3, i3);
+    }
+};
+
 // R = A * B split: n = na + A nb, k = kb + B ka.
 //   Y[na][kb] = DFT_B over nb of a[na + A nb];  Y[na][kb] *= W_R^{na kb};
 //   X[kb + B ka] = DFT_A over na of Y[na][kb].
@@ -204,6 +235,7 @@ __device__ __forceinline__ void dft_runtime(int R, float2* a)
     case 3: Dft<3, DIR>::run(a); break;
     case 4: Dft<4, DIR>::run(a); break;
     case 5: Dft<5, DIR>::run(a); break;
+    case 7: Dft<7, DIR>::run(a); break;
     case 8: Dft<8, DIR>::run(a); break;
     case 16: Dft<16, DIR>::run(a); break;
     default: break;

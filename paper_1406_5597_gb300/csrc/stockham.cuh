@@ -24,8 +24,8 @@ namespace fft3d {
 
 constexpr int pick_radix(int rem, int E)
 {
-    constexpr int order[7] = {32, 16, 8, 4, 2, 5, 3};
-    for (int i = 0; i < 7; ++i)
+    constexpr int order[8] = {32, 16, 8, 4, 2, 5, 3, 7};
+    for (int i = 0; i < 8; ++i)
         if (E % order[i] == 0 && rem % order[i] == 0) return order[i];
     return 0;
 }
@@ -117,7 +117,7 @@ struct RowExchange {
 template <int R>
 constexpr int n_powers()
 {
-    return R == 2 ? 1 : R == 3 || R == 4 ? 2 : R == 5 || R == 8 ? 3 : R == 16 ? 4 : 5;
+    return R == 2 ? 1 : R == 3 || R == 4 ? 2 : R == 5 || R == 7 || R == 8 ? 3 : R == 16 ? 4 : 5;
 }
 
 template <int R>
@@ -133,13 +133,11 @@ __device__ __forceinline__ void twiddle_set(const float2 (&p)[5], float2* w)
 {
     w[1] = p[0];
     if constexpr (R >= 3) w[2] = p[1];
-    if constexpr (R == 4 || R == 5 || R >= 8) w[3] = cmul(p[0], p[1]);
-    if constexpr (R == 5 || R >= 8) w[4] = p[2];
-    if constexpr (R >= 8) {
-        w[5] = cmul(w[1], w[4]);
-        w[6] = cmul(w[2], w[4]);
-        w[7] = cmul(w[3], w[4]);
-    }
+    if constexpr (R >= 4) w[3] = cmul(p[0], p[1]);
+    if constexpr (R >= 5) w[4] = p[2];
+    if constexpr (R >= 6) w[5] = cmul(w[1], w[4]);
+    if constexpr (R >= 7) w[6] = cmul(w[2], w[4]);
+    if constexpr (R >= 8) w[7] = cmul(w[3], w[4]);
     if constexpr (R == 16) {
         w[8] = p[3];
         const float2 w12 = cmul(w[4], w[8]);

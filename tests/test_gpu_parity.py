@@ -127,8 +127,10 @@ SHAPES = [
     (8, 6, 1024), (3, 2, 2048),
     # n1 pass through the TMA kernel: row pairs (odd H) with ragged tiles, plain rows (even H)
     (6, 512, 60), (3, 256, 40), (4, 1024, 30), (5, 256, 512), (1536, 4, 12),
-    # row pairs whose last column tile would hold one column (split off to the plain kernel)
+    # row pairs whose last column tile would hold one column
     (2, 512, 64), (3, 1024, 32), (2, 512, 512),
+    # a factor 7 on every axis (runtime-radix kernels, radix-7 codelet)
+    (14, 28, 56), (7, 7, 14), (49, 6, 28), (112, 3, 98), (5, 21, 70),
 ]
 
 

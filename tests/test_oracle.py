@@ -28,7 +28,7 @@ def rel_l2(a, b):
 
 TINY = [(n0, n1, n2) for n0, n1, n2 in itertools.product((2, 3, 4, 5, 6, 8, 10), (2, 3, 5, 6, 12),
                                                          (2, 4, 6, 10, 16))
-        if n0 * n1 * n2 <= 8192][::3] + [(6, 10, 16), (8, 8, 8), (15, 12, 10), (16, 16, 16)]
+        if n0 * n1 * n2 <= 8192][::3] + [(6, 10, 16), (8, 8, 8), (15, 12, 10), (16, 16, 16), (7, 6, 14), (14, 7, 4)]
 
 
 @pytest.mark.parametrize("shape", TINY)
