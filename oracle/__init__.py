@@ -12,8 +12,9 @@ spectrum (Parseval, shell energies, the 2/3 mask, the nonlinear term).
 Definitions (Sec. 2 of Chatterjee, Verma & Chaudhuri, arXiv:1406.5597, with
 the FFTW sign/scaling convention of the transforms the paper uses, Sec. 3):
 
-    r2c: X[k] = sum_j x[j] exp(-2 pi i (k0 j0/n0 + k1 j1/n1 + k2 j2/n2)), 0 <= k2 <= n2/2
-    c2r: y[j] = sum_{k2} c_k2 Re(sum_{k0,k1} Y[k] exp(+2 pi i (...))),  c_k2 = 1 at 0, n2/2 else 2
+    r2c: X[k] = sum_j x[j] exp(-2 pi i (k0 j0/n0 + k1 j1/n1 + k2 j2/n2)), 0 <= k2 <= floor(n2/2)
+    c2r: y[j] = sum_{k2} c_k2 Re(sum_{k0,k1} Y[k] exp(+2 pi i (...))),  c_k2 = 1 at 0 and at
+         n2/2 (even n2), else 2
 """
 from __future__ import annotations
 
@@ -173,12 +174,13 @@ def c2r_points_c64(Y64: np.ndarray, n2: int, jvecs) -> np.ndarray:
 # ---------------------------------------------------------------------------
 
 def half_weights(n2: int) -> np.ndarray:
-    """c_k2: 1 at k2 = 0 and k2 = n2/2, 2 in between (each interior bin stands
-    for itself and its conjugate partner)."""
+    """c_k2: 1 at k2 = 0 and, for even n2, at the Nyquist bin k2 = n2/2; 2 for
+    every other bin (it stands for itself and its conjugate partner)."""
     H = n2 // 2 + 1
     c = np.full(H, 2.0)
     c[0] = 1.0
-    c[H - 1] = 1.0
+    if n2 % 2 == 0:
+        c[H - 1] = 1.0
     return c
 
 

@@ -10,13 +10,15 @@
  * constant with the CUDA path.
  *
  * What it computes (Sec. 2): a real n0 x n1 x n2 array is transformed to the
- * non-redundant complex half n0 x n1 x (n2/2+1) ("r2c", forward), and back
+ * non-redundant complex half n0 x n1 x (n2/2+1) ("r2c", forward; n2/2 rounded
+ * down for odd n2), and back
  * ("c2r", inverse).  The paper fixes neither sign nor scaling; the reading
  * used here is the FFTW convention (the paper's transforms are FFTW's, Sec. 3):
  *
  *   X[k0,k1,k2] = sum_j x[j0,j1,j2] exp(-2 pi i (k0 j0/n0 + k1 j1/n1 + k2 j2/n2))
  *   y[j]        = sum_{k2=0}^{n2/2} c_k2 Re( sum_{k0,k1} Y[k] exp(+2 pi i (...)) )
- *                 with c_k2 = 1 at k2 in {0, n2/2}, else 2;  unnormalised.
+ *                 with c_k2 = 1 at k2 = 0 and (even n2) at k2 = n2/2, else 2;
+ *                 unnormalised.
  *
  * The forward transform follows the three steps of Sec. 2.1 in order: a 2D
  * transform of every n0-plane (here: axis n2, then axis n1) followed by the
@@ -180,7 +182,7 @@ static int axis_fft(cplx* v, size_t outer, int n, size_t inner, int sign)
  * X: batch*n0*n1*(n2/2+1) interleaved complex. */
 int oracle_r2c3d(const double* x, double* Xout, int n0, int n1, int n2, int batch)
 {
-    if (!x || !Xout || n0 < 1 || n1 < 1 || n2 < 2 || (n2 & 1) || batch < 1) return -1;
+    if (!x || !Xout || n0 < 1 || n1 < 1 || n2 < 2 || batch < 1) return -1;
     const int H = n2 / 2 + 1;
     const size_t rows = (size_t)batch * n0 * n1;
     cplx* X = (cplx*)Xout;
@@ -219,7 +221,7 @@ int oracle_r2c3d(const double* x, double* Xout, int n0, int n1, int n2, int batc
  * modified (the oracle works on a copy). */
 int oracle_c2r3d(const double* Yin, double* y, int n0, int n1, int n2, int batch)
 {
-    if (!Yin || !y || n0 < 1 || n1 < 1 || n2 < 2 || (n2 & 1) || batch < 1) return -1;
+    if (!Yin || !y || n0 < 1 || n1 < 1 || n2 < 2 || batch < 1) return -1;
     const int H = n2 / 2 + 1;
     const size_t rows = (size_t)batch * n0 * n1;
     cplx* A = (cplx*)malloc(sizeof(cplx) * rows * H);
@@ -230,7 +232,8 @@ int oracle_c2r3d(const double* Yin, double* y, int n0, int n1, int n2, int batch
     if ((err = axis_fft(A, (size_t)batch * n0, n1, (size_t)H, +1))) { free(A); return err; }
     /* Real synthesis along n2: y[j2] = sum_k2 c_k2 Re(A[k2] e^{+2 pi i k2 j2/n2}),
      * done as the inverse complex FFT of the Hermitian extension Z of the row:
-     * Z[0] = Re A[0], Z[n2/2] = Re A[n2/2], Z[k] = A[k], Z[n2-k] = conj A[k]. */
+     * Z[0] = Re A[0], Z[k] = A[k], Z[n2-k] = conj A[k] for 1 <= k <= (n2-1)/2,
+     * and for even n2 the Nyquist bin Z[n2/2] = Re A[n2/2]. */
     cplx* w = make_table(n2, +1);
     if (!w) { free(A); return -2; }
     err = 0;
@@ -246,8 +249,8 @@ int oracle_c2r3d(const double* Yin, double* y, int n0, int n1, int n2, int batch
             for (long long r = 0; r < (long long)rows; ++r) {
                 const cplx* Ar = A + (size_t)r * H;
                 row[0] = creal(Ar[0]);
-                row[n2 / 2] = creal(Ar[n2 / 2]);
-                for (int k = 1; k < n2 / 2; ++k) {
+                if ((n2 & 1) == 0) row[n2 / 2] = creal(Ar[n2 / 2]);
+                for (int k = 1; k <= (n2 - 1) / 2; ++k) {
                     row[k] = Ar[k];
                     row[n2 - k] = conj(Ar[k]);
                 }
@@ -293,7 +296,7 @@ static void kahan_add(kahan_c* k, cplx v)
 /* X[k] for every k in the half spectrum, straight from the definition. */
 int oracle_r2c3d_naive(const double* x, double* Xout, int n0, int n1, int n2)
 {
-    if (!x || !Xout || n0 < 1 || n1 < 1 || n2 < 2 || (n2 & 1)) return -1;
+    if (!x || !Xout || n0 < 1 || n1 < 1 || n2 < 2) return -1;
     if ((long long)n0 * n1 * n2 > 8192) return -1; /* O(N^2): tiny shapes only */
     const int H = n2 / 2 + 1;
     cplx* X = (cplx*)Xout;
@@ -316,7 +319,7 @@ int oracle_r2c3d_naive(const double* x, double* Xout, int n0, int n1, int n2)
 /* y[j] = sum_{k2<=n2/2} c_k2 Re(sum_{k0,k1} Y[k] exp(+...)), straight from the definition. */
 int oracle_c2r3d_naive(const double* Yin, double* y, int n0, int n1, int n2)
 {
-    if (!Yin || !y || n0 < 1 || n1 < 1 || n2 < 2 || (n2 & 1)) return -1;
+    if (!Yin || !y || n0 < 1 || n1 < 1 || n2 < 2) return -1;
     if ((long long)n0 * n1 * n2 > 8192) return -1;
     const int H = n2 / 2 + 1;
     const cplx* Y = (const cplx*)Yin;
@@ -352,7 +355,7 @@ int oracle_c2r3d_naive(const double* Yin, double* y, int n0, int n1, int n2)
 int oracle_r2c_bins_f32(const float* x, int n0, int n1, int n2,
                         const int* k, int nb, double* out)
 {
-    if (!x || !k || !out || n0 < 1 || n1 < 1 || n2 < 2 || (n2 & 1) || nb < 0) return -1;
+    if (!x || !k || !out || n0 < 1 || n1 < 1 || n2 < 2 || nb < 0) return -1;
     for (int b = 0; b < nb; ++b)
         if (k[3*b] < 0 || k[3*b] >= n0 || k[3*b+1] < 0 || k[3*b+1] >= n1 ||
             k[3*b+2] < 0 || k[3*b+2] > n2 / 2) return -1;
@@ -389,7 +392,7 @@ int oracle_r2c_bins_f32(const float* x, int n0, int n1, int n2,
 int oracle_c2r_points_c64(const float* Yf, int n0, int n1, int n2,
                           const int* j, int np, double* out)
 {
-    if (!Yf || !j || !out || n0 < 1 || n1 < 1 || n2 < 2 || (n2 & 1) || np < 0) return -1;
+    if (!Yf || !j || !out || n0 < 1 || n1 < 1 || n2 < 2 || np < 0) return -1;
     for (int p = 0; p < np; ++p)
         if (j[3*p] < 0 || j[3*p] >= n0 || j[3*p+1] < 0 || j[3*p+1] >= n1 ||
             j[3*p+2] < 0 || j[3*p+2] >= n2) return -1;

@@ -28,7 +28,8 @@ def rel_l2(a, b):
 
 TINY = [(n0, n1, n2) for n0, n1, n2 in itertools.product((2, 3, 4, 5, 6, 8, 10), (2, 3, 5, 6, 12),
                                                          (2, 4, 6, 10, 16))
-        if n0 * n1 * n2 <= 8192][::3] + [(6, 10, 16), (8, 8, 8), (15, 12, 10), (16, 16, 16), (7, 6, 14), (14, 7, 4)]
+        if n0 * n1 * n2 <= 8192][::3] + [(6, 10, 16), (8, 8, 8), (15, 12, 10), (16, 16, 16), (7, 6, 14), (14, 7, 4),
+                                          (4, 6, 9), (5, 3, 15), (6, 8, 7), (3, 5, 3), (2, 2, 21)]
 
 
 @pytest.mark.parametrize("shape", TINY)
@@ -66,7 +67,8 @@ def test_fft1d_matches_numpy(n):
     assert rel_l2(oracle.fft1d(x, +1), n * np.fft.ifft(x)) < 1e-13
 
 
-@pytest.mark.parametrize("shape", [(32, 32, 32), (6, 10, 16), (15, 12, 10), (64, 48, 40), (2, 2, 2)])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (6, 10, 16), (15, 12, 10), (64, 48, 40), (2, 2, 2), (16, 12, 45),
+                                   (8, 10, 27)])
 def test_r2c_matches_numpy_rfftn(shape):
     x = synth.uniform_field(shape, seed=3)
     assert rel_l2(oracle.r2c3d(x), np.fft.rfftn(x)) < 1e-13
@@ -355,3 +357,23 @@ def test_ns_rhs_conserves_energy_without_viscosity_and_is_solenoidal():
     rate = np.sum(w * np.real(np.conj(uh) * R))
     expect = -nu * np.sum(w * kk * np.abs(uh) ** 2)
     assert abs(rate - expect) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("n2", [9, 15, 21, 25])
+def test_odd_n2_half_spectrum_invariants(n2):
+    """Odd n2: H = (n2 + 1) / 2 bins, no Nyquist bin, so every bin but k2 = 0
+    counts twice in Parseval and in the synthesis; the round trip is x N and
+    the imaginary part of the last bin does matter (it is not a Nyquist bin)."""
+    shape = (6, 5, n2)
+    N = 6 * 5 * n2
+    x = synth.uniform_field(shape, seed=n2)
+    X = oracle.r2c3d(x)
+    assert X.shape[-1] == (n2 + 1) // 2
+    assert abs(oracle.half_energy(X, n2) / N - np.sum(x ** 2)) <= 1e-12 * np.sum(x ** 2)
+    assert rel_l2(oracle.c2r3d(X, n2), N * x) < 1e-13
+    Y = np.zeros_like(X)
+    Y[0, 0, -1] = 1j  # sin(2 pi k2 j2 / n2) with weight 2 at the top bin
+    k2 = X.shape[-1] - 1
+    j2 = np.arange(n2)
+    expect = np.broadcast_to(-2 * np.sin(2 * np.pi * k2 * j2 / n2), shape)
+    assert np.max(np.abs(oracle.c2r3d(Y, n2) - expect)) < 1e-13
