@@ -60,7 +60,7 @@ typedef enum {
 typedef enum {
     FFT3D_OK = 0,
     FFT3D_ERR_INVALID_ARG = 1,      /* NULL/overlapping pointers, bad enum, n < 1, batch < 1 */
-    FFT3D_ERR_UNSUPPORTED_SIZE = 2, /* odd n2, a prime factor other than 2, 3, 5, 7, or too long an axis */
+    FFT3D_ERR_UNSUPPORTED_SIZE = 2, /* a prime factor other than 2, 3, 5, 7, or too long an axis */
     FFT3D_ERR_MISALIGNED = 3,       /* a data pointer not 16-byte aligned */
     FFT3D_ERR_ALLOC = 4,            /* plan-time device allocation failed */
     FFT3D_ERR_CUDA = 5,             /* a CUDA call or launch failed */
@@ -97,9 +97,10 @@ typedef enum {
 
 /*
  * Create a plan for batch transforms of size n0 x n1 x n2 (Sec. 2).
- * Requirements: n0, n1 >= 1, n2 >= 2 and even (H = n2/2+1 presumes it), every
- * prime factor of n0, n1 and n2/2 in {2, 3, 5, 7} (lengths with a factor 7 run the
- * runtime-radix kernels), no axis longer than 4096,
+ * Requirements: n0, n1 >= 1, n2 >= 2, every prime factor of n0, n1 and of the
+ * row transform length (n2/2 for even n2, n2 for odd n2) in {2, 3, 5, 7}
+ * (lengths with a factor 7, and odd n2, run the runtime-radix kernels), no
+ * transform longer than 4096, H = floor(n2/2) + 1 (no Nyquist bin for odd n2),
  * batch >= 1, and a current CUDA device.  Chooses the passes and the kernel
  * shapes, computes twiddle tables in FP64 on the host, rounds them to FP32 and
  * copies them to the device.  Blocks.  Returns NULL on error (reason in

@@ -194,7 +194,7 @@ struct fft3d_plan_s {
     int n0 = 0, n1 = 0, n2 = 0, H = 0, batch = 0, dtype = 0, flags = 0;
     long long N = 0, M = 0, P = 0;
     int device = 0;
-    Axis ax0, ax1, ax2;  // ax2: length n2/2 (row transform)
+    Axis ax0, ax1, ax2;  // ax2: the row transform, length n2/2 (even n2) or n2 (odd n2)
     float2* d_twpack = nullptr;
     int* d_status = nullptr;
     const PlaneEntry* plane = nullptr;  // fused n2+n1 kernel, when one fits this shape
@@ -357,7 +357,13 @@ cudaError_t run_row(fft3d_plan_s* p, int dir, const void* in, void* out, cudaStr
 {
     ProfScope ps(p, dir < 0 ? PASS_ROW_R2C : PASS_ROW_C2R, s);
     // real rows: n2 floats, or 2H floats in the padded (in-place capable) layout
-    const long long rs = (p->flags & FFT3D_FLAG_PADDED_REAL) ? p->H : p->n2 / 2;
+    const bool padded = p->flags & FFT3D_FLAG_PADDED_REAL;
+    if (p->n2 & 1) {  // odd n2: full-length complex row transform, stride in floats
+        RowArgs ra{in, out, (long long)p->batch * p->n0 * p->n1, p->ax2.d_tw, p->d_twpack,
+                   padded ? 2 * p->H : (long long)p->n2};
+        return generic_row_odd(ra, p->ax2.gen, dir, s);
+    }
+    const long long rs = padded ? p->H : p->n2 / 2;
     RowArgs ra{in, out, (long long)p->batch * p->n0 * p->n1, p->ax2.d_tw, p->d_twpack, rs};
     if (uses_generic(p, p->ax2, true)) return generic_row(ra, p->ax2.gen, dir, s);
     return dir < 0 ? p->ax2.spec->r2c(ra, p->choice_rows, s) : p->ax2.spec->c2r(ra, p->choice_rows, s);
@@ -433,7 +439,7 @@ const CPlaneEntry* cplane_for(int LR, int LC, int C)
 // The plan may replace its row and n1 passes by a cluster plane pass.
 bool cplane_allowed(const fft3d_plan_s* p)
 {
-    return p->dtype == FFT3D_F32 && !p->plane &&
+    return p->dtype == FFT3D_F32 && !p->plane && (p->n2 % 2 == 0) &&
            !(p->flags & (FFT3D_FLAG_THREE_PASS | FFT3D_FLAG_GENERIC | FFT3D_FLAG_EXPLICIT_TRANSPOSE |
                          FFT3D_FLAG_FUSED_PLANE | FFT3D_FLAG_PADDED_REAL));
 }
@@ -503,7 +509,7 @@ const char* fft3d_error_string(int status)
     switch (status) {
     case FFT3D_OK: return "ok";
     case FFT3D_ERR_INVALID_ARG: return "invalid argument";
-    case FFT3D_ERR_UNSUPPORTED_SIZE: return "unsupported size (n2 must be even; n0, n1, n2/2 must be 2,3,5,7-smooth and <= 4096)";
+    case FFT3D_ERR_UNSUPPORTED_SIZE: return "unsupported size (n0, n1 and n2/2 (n2 for odd n2) must be 2,3,5,7-smooth and <= 4096)";
     case FFT3D_ERR_MISALIGNED: return "data pointer not 16-byte aligned";
     case FFT3D_ERR_ALLOC: return "device allocation failed";
     case FFT3D_ERR_CUDA: return "CUDA error";
@@ -528,8 +534,10 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
         fail(FFT3D_ERR_INVALID_ARG);
         return nullptr;
     }
-    if ((n2 & 1) || !smooth2357(n0) || !smooth2357(n1) || !smooth2357(n2 / 2) || n0 > kMaxAxis || n1 > kMaxAxis ||
-        n2 / 2 > kMaxAxis) {
+    // the row transform has length n2/2 (even n2, half-length packing) or n2 (odd n2)
+    const int row_len = (n2 & 1) ? n2 : n2 / 2;
+    if (!smooth2357(n0) || !smooth2357(n1) || !smooth2357(row_len) || n0 > kMaxAxis || n1 > kMaxAxis ||
+        row_len > kMaxAxis) {
         fail(FFT3D_ERR_UNSUPPORTED_SIZE);
         return nullptr;
     }
@@ -559,11 +567,11 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
         return nullptr;
     }
     Axis* axes[3] = {&p->ax0, &p->ax1, &p->ax2};
-    const int lens[3] = {n0, n1, n2 / 2};
+    const int lens[3] = {n0, n1, row_len};
     for (int i = 0; i < 3; ++i) {
         Axis& a = *axes[i];
         a.L = lens[i];
-        a.spec = find_len(a.L);
+        a.spec = (i == 2 && (n2 & 1)) ? nullptr : find_len(a.L);  // odd rows: the runtime-length kernel
         a.tc = (dtype != FFT3D_F32 && i < 2) ? find_tc(a.L) : nullptr;
         a.gen = generic_radices(a.L);
         if (a.L >= 1) {
@@ -604,7 +612,7 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
         int np = 0;
         const PlaneEntry* pe = plane_entries(&np);
         for (int i = 0; i < np; ++i)
-            if (pe[i].LR == n2 / 2 && pe[i].LC == n1) p->plane = &pe[i];
+            if (n2 % 2 == 0 && pe[i].LR == n2 / 2 && pe[i].LC == n1) p->plane = &pe[i];
         // per-plane counters, then an 8-byte work ticket (kept 8-byte aligned)
         const size_t ncount = (((size_t)batch * n0 + 1) & ~(size_t)1) + 2;
         if (p->plane && cudaMalloc((void**)&p->d_counters, ncount * sizeof(int)) != cudaSuccess) {

@@ -40,7 +40,8 @@ struct RowArgs {
     long long rows;
     const float2* tw;      // W_L^m, m in [0, L), L = n2/2
     const float2* twpack;  // exp(-2 pi i k / n2), k in [0, L]
-    long long rs;          // real-side row stride in float pairs: L (dense) or L + 1 (padded rows of 2H floats)
+    long long rs;          // real-side row stride: in float pairs for even n2, L (dense) or L + 1 (padded
+                           // rows of 2H floats); in floats for odd n2 (n2 dense, 2H = n2 + 1 padded)
 };
 
 // Runtime radix plan for the generic (any 2/3/5-smooth length) kernels.
@@ -105,5 +106,6 @@ const TcEntry* tc_entries(int* n);
 // Generic kernels: dir = -1 forward, +1 inverse.
 cudaError_t generic_col(const ColArgs& a, const GenPlan& g, int dir, cudaStream_t s);
 cudaError_t generic_row(const RowArgs& a, const GenPlan& g, int dir, cudaStream_t s);
+cudaError_t generic_row_odd(const RowArgs& a, const GenPlan& g, int dir, cudaStream_t s);
 
 }  // namespace fft3d

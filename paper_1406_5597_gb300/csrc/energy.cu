@@ -5,7 +5,7 @@
 //
 // For X of shape batch x n0 x n1 x H (H = n2/2+1), per batch entry:
 //   total    = sum over the half spectrum of c_k2 |X[k]|^2,
-//              c_k2 = 1 at k2 = 0 and k2 = n2/2, else 2  (= N sum_j x_j^2 when X = r2c(x));
+//              c_k2 = 1 at k2 = 0 and (even n2) k2 = n2/2, else 2  (= N sum_j x_j^2 when X = r2c(x));
 //   shell[b] = the same sum restricted to the bins whose integer shell is b,
 //              b = floor(|k| + 1/2) with |k_a| = min(j_a, n_a - j_a): shell 0
 //              is k = 0 alone, shell b >= 1 is (2b-1)^2 <= 4|k|^2 < (2b+1)^2,

@@ -1,5 +1,5 @@
-// Runtime-length kernels: any transform length whose prime factors are 2, 3
-// and 5 (up to 4096), for the axis lengths that have no compile-time
+// Runtime-length kernels: any transform length whose prime factors are 2, 3,
+// 5 and 7 (up to 4096), for the axis lengths that have no compile-time
 // specialisation.  A CTA stages G lines in shared memory (two buffers) and
 // runs the Stockham stages of a runtime radix list, one butterfly per thread
 // iteration.  Same mathematics as the specialised kernels (see stockham.cuh
@@ -152,6 +152,60 @@ __global__ void generic_row_kernel(RowArgs a, GenPlan g, int G)
     }
 }
 
+// Rows of odd length n2 = g.L (no half-length packing): the r2c is the
+// length-n2 complex FFT of the real row (imaginary parts zero), bins
+// 0 .. (n2-1)/2 kept; the c2r builds the Hermitian extension of the
+// (n2+1)/2 bins (Im of the DC bin dropped, no Nyquist bin) and keeps the real
+// part of its length-n2 inverse FFT.  Real rows at a stride of a.rs floats.
+template <int DIR>
+__global__ void generic_row_odd_kernel(RowArgs a, GenPlan g, int G)
+{
+    extern __shared__ float2 sm[];
+    const int L = g.L, H = L / 2 + 1;
+    float2* b0 = sm;
+    float2* b1 = sm + (size_t)(L + 1) * G;
+    const long long row0 = (long long)blockIdx.x * G;
+    const int nrows = (int)min((long long)G, a.rows - row0);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthr = blockDim.x * blockDim.y;
+    if (DIR < 0) {
+        const float* in = reinterpret_cast<const float*>(a.in) + row0 * a.rs;
+        for (int i = tid; i < L * G; i += nthr) {
+            const int line = i / L, p = i % L;
+            b0[gi(p, line, G)] = make_float2(line < nrows ? in[line * a.rs + p] : 0.f, 0.f);
+        }
+        __syncthreads();
+        float2* X = generic_stages<-1>(g, b0, b1, G, a.tw);
+        float2* out = reinterpret_cast<float2*>(a.out) + row0 * H;
+        for (int i = tid; i < H * nrows; i += nthr) {
+            const int line = i / H, k = i % H;
+            out[i] = X[gi(k, line, G)];
+        }
+    } else {
+        const float2* in = reinterpret_cast<const float2*>(a.in) + row0 * H;
+        for (int i = tid; i < L * G; i += nthr) {
+            const int line = i / L, k = i % L;
+            float2 v = make_float2(0.f, 0.f);
+            if (line < nrows) {
+                if (k < H) {
+                    v = in[line * H + k];
+                    if (k == 0) v.y = 0.f;
+                } else {
+                    v = cconj(in[line * H + (L - k)]);
+                }
+            }
+            b0[gi(k, line, G)] = v;
+        }
+        __syncthreads();
+        float2* y = generic_stages<+1>(g, b0, b1, G, a.tw);
+        float* out = reinterpret_cast<float*>(a.out) + row0 * a.rs;
+        for (int i = tid; i < L * nrows; i += nthr) {
+            const int line = i / L, p = i % L;
+            out[line * a.rs + p] = y[gi(p, line, G)].x;
+        }
+    }
+}
+
 int lines_per_cta(int L)
 {
     const int cap = 64 * 1024;  // bytes of shared memory for both buffers
@@ -176,6 +230,23 @@ cudaError_t generic_col(const ColArgs& a, const GenPlan& g, int dir, cudaStream_
     } else {
         cudaFuncSetAttribute(generic_col_kernel<+1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         generic_col_kernel<+1><<<(unsigned)tiles, block, smem, s>>>(a, g, G);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t generic_row_odd(const RowArgs& a, const GenPlan& g, int dir, cudaStream_t s)
+{
+    const int G = lines_per_cta(g.L);
+    const size_t smem = 2 * (size_t)(g.L + 1) * G * sizeof(float2);
+    const long long blocks = (a.rows + G - 1) / G;
+    if (blocks <= 0) return cudaSuccess;
+    dim3 block(G, 256 / G > 0 ? 256 / G : 1);
+    if (dir < 0) {
+        cudaFuncSetAttribute(generic_row_odd_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        generic_row_odd_kernel<-1><<<(unsigned)blocks, block, smem, s>>>(a, g, G);
+    } else {
+        cudaFuncSetAttribute(generic_row_odd_kernel<+1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        generic_row_odd_kernel<+1><<<(unsigned)blocks, block, smem, s>>>(a, g, G);
     }
     return cudaGetLastError();
 }

@@ -30,7 +30,7 @@ def test_error_strings(lib):
 @pytest.mark.parametrize("dims,status", [
     ((0, 8, 8), fft3d.FFT3D_ERR_INVALID_ARG),
     ((8, 8, 1), fft3d.FFT3D_ERR_INVALID_ARG),
-    ((8, 8, 7), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),   # odd n2
+    ((8, 8, 11), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),  # odd n2 with a factor 11
     ((22, 8, 8), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),  # factor 11
     ((8, 8, 22), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),  # n2/2 = 11
     ((8192, 8, 8), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),
@@ -53,7 +53,7 @@ def test_plan_rejects_bad_dtype_batch_flags(lib):
 
 
 def test_nonlinear_plan_rejects_bad_sizes(lib):
-    assert not fft3d.fft3d_nonlinear_plan(8, 8, 7)
+    assert not fft3d.fft3d_nonlinear_plan(8, 8, 11)
     assert fft3d.fft3d_last_error() == fft3d.FFT3D_ERR_UNSUPPORTED_SIZE
     assert fft3d.fft3d_nonlinear_exec(None, 16, 32) == fft3d.FFT3D_ERR_INVALID_ARG
     assert fft3d.fft3d_nonlinear_workspace_bytes(None) == 0

@@ -131,6 +131,8 @@ SHAPES = [
     (2, 512, 64), (3, 1024, 32), (2, 512, 512),
     # a factor 7 on every axis (runtime-radix kernels, radix-7 codelet)
     (14, 28, 56), (7, 7, 14), (49, 6, 28), (112, 3, 98), (5, 21, 70),
+    # odd n2 (full-length row transforms, no Nyquist bin)
+    (8, 6, 15), (4, 10, 9), (5, 3, 21), (16, 16, 45), (3, 7, 35), (6, 4, 3), (32, 32, 27), (2, 2, 875),
 ]
 
 
@@ -263,7 +265,7 @@ def test_plane_form_every_cluster_size_and_autotune(cuda_lib, shape):
 
 
 PADDED_SHAPES = [(32, 32, 32), (64, 64, 64), (6, 512, 60), (8, 6, 1024), (3, 2, 2048), (2, 3, 4096), (48, 80, 96),
-                 (5, 3, 2), (1, 8, 16)]
+                 (5, 3, 2), (1, 8, 16), (4, 6, 9), (3, 5, 15)]
 
 
 @pytest.mark.parametrize("extra", ["plain", "generic", "tc"])
@@ -412,6 +414,21 @@ def test_navier_stokes_rejects_bad_arguments(cuda_lib):
     assert lib.fft3d_ns_step(h, u.data_ptr(), 0.01, 0.1, 0) == lib.FFT3D_OK
     torch.cuda.synchronize()
     lib.fft3d_ns_destroy(h)
+
+
+@pytest.mark.parametrize("shape", [(8, 6, 15), (6, 10, 32)], ids=lambda s: "x".join(map(str, s)))
+def test_energy_weights_follow_n2_parity(cuda_lib, shape):
+    """Parseval on the device: the last bin weighs 1 only when it is a Nyquist
+    bin (even n2)."""
+    n0, n1, n2 = shape
+    x32 = synth.uniform_field(shape, seed=95).astype(np.float32)
+    plan = cuda_lib.Plan(n0, n1, n2)
+    X = torch.empty((n0, n1, n2 // 2 + 1), dtype=torch.complex64, device="cuda")
+    plan.r2c(torch.from_numpy(x32).cuda().data_ptr(), X.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    total, _ = plan.energy(X, 4)
+    ref = oracle.half_energy(X.cpu().numpy(), n2)
+    assert abs(total.item() - ref) <= 1e-9 * ref
+    assert abs(total.item() / (n0 * n1 * n2) - np.sum(x32.astype(np.float64) ** 2)) <= 1e-5 * ref / (n0 * n1 * n2)
 
 
 def test_bounded_wait_gives_up_without_hanging(cuda_lib):
