@@ -389,8 +389,8 @@ std::string axis_desc(const fft3d_plan_s* p, const Axis& a, bool row)
     } else if (const int mode = (&a == &p->ax0) ? (p->choice_tma ? tma_mode(p, a, p->P, p->P, p->M) : 0)
                                                 : (p->choice_tma1 ? tma_mode(p, a, p->H, p->H, (long long)p->n1 * p->H)
                                                                   : 0)) {
-        std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d %s", a.L, a.spec->tma_E, a.spec->tma_W,
-                      mode == 2 ? "tma-row-pairs" : "tma");
+        std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d %s", a.L, mode == 2 ? a.spec->tma_pair_E : a.spec->tma_E,
+                      a.spec->tma_W, mode == 2 ? "tma-row-pairs" : "tma");
     } else {
         const int w = (&a == &p->ax0) ? p->choice_w0 : p->choice_w1;
         std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d", a.L, a.spec->col_E,

@@ -76,6 +76,7 @@ struct LenEntry {
     int tma_E, tma_W;  // TMA-fed persistent column kernel (tma_W = 0: none)
     ColTmaFn tma_fwd, tma_inv;
     ColTmaFn tma_pair_fwd, tma_pair_inv;  // same, for an odd axis stride (row-pair view)
+    int tma_pair_E;                       // its elements per thread
     int row_E, row_rows;  // row kernels (row_E = 0: none)
     bool row_warp;        // rows resident in warps (shuffle unpack) or staged in shared memory
     RowFn r2c, c2r;

@@ -5,7 +5,7 @@ namespace fft3d {
 const LenEntry* entries_1024_2048(int* n)
 {
     static const LenEntry e[] = {
-        {1024, FFT3D_COL(1024, 32, 16), FFT3D_TMA(1024, 16, 8, 2, 0, 2, 2), FFT3D_ROWW_NONL(1024, 32, 2)},
+        {1024, FFT3D_COL(1024, 32, 16), FFT3D_TMA(1024, 16, 8, 2, 0, 16, 2, 2), FFT3D_ROWW_NONL(1024, 32, 2)},
         {2048, FFT3D_COL(2048, 32, 8), FFT3D_NO_TMA, FFT3D_NO_ROW},
     };
     *n = (int)(sizeof(e) / sizeof(e[0]));
