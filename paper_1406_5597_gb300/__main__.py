@@ -2,16 +2,19 @@
 random data on the current CUDA device, through the C ABI.
 
     python -m paper_1406_5597_gb300 --shape 512,512,512 [--flags 0x40] [--dtype f32|bf16x3|f16]
+    python -m paper_1406_5597_gb300 --shape 256,256,256 --ns
 
 Prints the plan description and the round-trip relative L2 error
-(c2r(r2c(x)) / N against x).  Useful as the target of a profiler run: it
-launches exactly the kernels of one transform pair.
+(c2r(r2c(x)) / N against x).  With --ns it instead runs one pseudo-spectral
+Navier-Stokes step (fft3d_ns_step, direct launches) on random spectra.  Useful
+as the target of a profiler run: it launches exactly the kernels of one
+transform pair (or one step).
 """
 import argparse
 
 import torch
 
-from . import FFT3D_F32, FFT3D_F32_TC_BF16X3, FFT3D_F32_TC_F16, Plan, load
+from . import FFT3D_F32, FFT3D_F32_TC_BF16X3, FFT3D_F32_TC_F16, NavierStokes, Plan, load
 
 
 def main() -> None:
@@ -21,6 +24,7 @@ def main() -> None:
     ap.add_argument("--flags", type=lambda v: int(v, 0), default=0, help="FFT3D_FLAG_* bits")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16x3", "f16"])
     ap.add_argument("--seed", type=int, default=1408)
+    ap.add_argument("--ns", action="store_true", help="one Navier-Stokes step instead of r2c + c2r")
     args = ap.parse_args()
     n0, n1, n2 = (int(v) for v in args.shape.split(","))
     dtype = {"f32": FFT3D_F32, "bf16x3": FFT3D_F32_TC_BF16X3, "f16": FFT3D_F32_TC_F16}[args.dtype]
@@ -28,6 +32,14 @@ def main() -> None:
     dev = torch.device("cuda", torch.cuda.current_device())
     gen = torch.Generator(device=dev)
     gen.manual_seed(args.seed)
+    if args.ns:
+        ns = NavierStokes(n0, n1, n2)
+        u = torch.randn((3, n0, n1, n2 // 2 + 1), dtype=torch.complex64, device=dev, generator=gen)
+        ns.step(u, 0.01, 1e-3, stream=False)
+        torch.cuda.synchronize(dev)
+        print(f"one Navier-Stokes step at {n0}x{n1}x{n2}: |u| = {float(u.abs().norm()):.6e}")
+        ns.close()
+        return
     lead = (args.batch,) if args.batch > 1 else ()
     x = torch.randn(lead + (n0, n1, n2), device=dev, generator=gen)
     X = torch.empty(lead + (n0, n1, n2 // 2 + 1), dtype=torch.complex64, device=dev)
