@@ -84,9 +84,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(pass_name, n):
-    """dram bytes per launch of a pass, from the committed ncu summary, if it
-    was taken on the current kernel sources (else None)."""
+def traffic_from_profile(pass_name, shape):
+    """dram bytes per launch of a pass at this shape ("n0xn1xn2"), from the
+    committed ncu summary, if it was taken on the current kernel sources
+    (else None)."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(p):
         return None
@@ -95,7 +96,7 @@ def traffic_from_profile(pass_name, n):
         if line.startswith("#") or not line.strip():
             continue
         kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
-        if kv.get("pass") == pass_name and kv.get("n") == str(n) and kv.get("src") == src:
+        if kv.get("pass") == pass_name and kv.get("shape") == shape and kv.get("src") == src:
             return float(kv["bytes_per_launch"])
     return None
 
@@ -312,7 +313,7 @@ def main():
     peak, peak_kind = measured_peak_hbm()
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_from_profile(dom, n), "kernel": dom, "peak_source": peak_kind,
+                "traffic": traffic_from_profile(dom, f"{n0}x{n1}x{n2}"), "kernel": dom, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms}
     passes = {k: {"avg_ms": v[0] / v[1], "launches": v[1],
                   "gbs": fft3d.fft3d_pass_bytes(plan.handle, names.index(k)) / (v[0] / v[1] * 1e-3) / 1e9}
