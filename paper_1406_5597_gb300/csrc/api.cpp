@@ -1361,7 +1361,11 @@ fft3d_group_handle fft3d_plan_group(const int* dims, const int* counts, int ngro
         return nullptr;
     }
     for (int i = 0; i < ngroups; ++i) {
-        fft3d_handle p = fft3d_plan(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], dtype, counts[i]);
+        // the sizes of a group run concurrently on their own streams: their
+        // plans keep the separate row and column passes (a persistent cluster
+        // plane kernel, tuned alone, would hold every SM and serialise them)
+        fft3d_handle p = fft3d_plan_variant(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], dtype, counts[i],
+                                            FFT3D_FLAG_THREE_PASS);
         if (!p) {
             const int st = fft3d_last_error();
             group_free(g);

@@ -109,13 +109,16 @@ struct CPlaneGeom {
     static constexpr int TR = LR / ER;                     // threads per row transform
     static constexpr int RPR = NT / TR;                    // rows per round (round 0 comes through the stage)
     static constexpr int ROUNDS = RC / RPR;
-    static constexpr int EC = RC >= 16 ? 16 : RC;          // column transform: elements per thread
+    static constexpr int EC = (RC <= 32 && num_stages(RC, RC) == 1) ? RC : 16;  // column transform: elements
+                                                           // per thread (one thread per column when a single
+                                                           // stage covers RC)
     static constexpr int TC = RC / EC;                     // threads per column
     static constexpr int GC = 32 / TC;                     // columns per warp
     static constexpr int NG = (H + GC - 1) / GC;           // column groups
     static constexpr int NW = NT / 32;
-    static constexpr int KPC = RC / C;                     // k' rows per CTA in the radix-C step
-    static constexpr int NX = KPC * H;                     // radix-C items per CTA
+    static constexpr int KPC = RC / C;                     // k' rows per CTA in the radix-C step (at least;
+                                                           // CTA q takes [q*RC/C, (q+1)*RC/C))
+    static constexpr int NX = KPC * H;                     // radix-C items of the smallest share
     static constexpr int XI = NX / NT;                     // items every thread takes (the rest: a tail)
     static constexpr int XP0 = XI < 16 / C ? XI : 16 / C;  // inverse: items loaded one plane ahead
     static constexpr int XPRE = XP0 > 0 ? XP0 : (XI > 0 ? 1 : 0);  // (at most 16 values in registers)
@@ -125,7 +128,7 @@ struct CPlaneGeom {
     static constexpr unsigned SLAB_LOAD_BYTES = (RC - RPR) * ROW_BYTES;
     static constexpr size_t smem_fwd = (size_t)SLAB * sizeof(float2) + STAGE_BYTES + 2 * sizeof(unsigned long long);
     static constexpr size_t smem_inv = (size_t)SLAB * sizeof(float2);
-    static_assert(LC % C == 0 && RC % C == 0, "n1 must split evenly over the cluster");
+    static_assert(LC % C == 0 && RC >= C, "n1 must split evenly over the cluster");
     static_assert(TR <= 32 && 32 % TR == 0 && NT % 32 == 0, "rows must pack into warps");
     static_assert(RPR <= RC && RC % RPR == 0, "row rounds must tile the slab rows");
     static_assert(RC % EC == 0 && TC <= 32 && 32 % TC == 0, "column transform must pack into warps");
@@ -140,7 +143,7 @@ __global__ void __launch_bounds__(NT, MINB) cplane_kernel(CPlaneArgs a)
 {
     using G = CPlaneGeom<LR, ER, LC, C, NT>;
     constexpr int H = G::H, RC = G::RC, SH = G::SH, TR = G::TR, RPR = G::RPR;
-    constexpr int EC = G::EC, TC = G::TC, GC = G::GC, KPC = G::KPC, NX = G::NX, XI = G::XPRE;
+    constexpr int EC = G::EC, TC = G::TC, GC = G::GC, XI = G::XPRE;
     extern __shared__ __align__(1024) unsigned char smraw[];
     float2* slab = reinterpret_cast<float2*>(smraw);
     const unsigned rank = cluster_ctarank();
@@ -149,7 +152,9 @@ __global__ void __launch_bounds__(NT, MINB) cplane_kernel(CPlaneArgs a)
     unsigned rs[C];  // the slabs of the cluster's CTAs, as shared::cluster addresses
 #pragma unroll
     for (int b = 0; b < C; ++b) rs[b] = dsmem_map(slab, (unsigned)b);
-    const int kbase = (int)rank * KPC;
+    // this CTA's k' rows in the radix-C step
+    const int kbase = (int)rank * RC / C;
+    const int NX = ((int)rank + 1) * RC / C * H - kbase * H;
     // row rounds: thread (rr, tr) transforms slab row r*RPR + rr
     const int rr = tid / TR, tr = tid - (tid / TR) * TR;
     // column groups: lane (cc, tc) of a warp, GC columns per group

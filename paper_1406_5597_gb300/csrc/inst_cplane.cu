@@ -19,6 +19,9 @@ const CPlaneEntry* cplane_entries(int* n)
         FFT3D_CPLANE(128, 8, 256, 4, 256, 2),   // 256^3: 4 CTAs x 64 rows
         FFT3D_CPLANE(128, 8, 256, 2, 512, 1),   // 256^3: 2 CTAs x 128 rows
         FFT3D_CPLANE(256, 16, 512, 8, 512, 1),  // 512^3: 8 CTAs x 64 rows
+        FFT3D_CPLANE(48, 12, 96, 3, 128, 2),    // 96^3: 3 CTAs x 32 rows
+        FFT3D_CPLANE(80, 20, 160, 5, 128, 2),   // 160^3: 5 CTAs x 32 rows
+        FFT3D_CPLANE(96, 24, 192, 3, 256, 2),   // 192^3: 3 CTAs x 64 rows
     };
     *n = (int)(sizeof(e) / sizeof(e[0]));
     return e;

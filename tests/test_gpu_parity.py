@@ -224,7 +224,8 @@ def _plan_r2c_c2r(lib, plan, x32, Y64, n2):
     return X.cpu().numpy().astype(np.complex128), y.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("shape", [(9, 32, 32), (10, 64, 64), (5, 128, 128), (6, 256, 256), (3, 512, 512)],
+@pytest.mark.parametrize("shape", [(9, 32, 32), (10, 64, 64), (5, 128, 128), (6, 256, 256), (3, 512, 512),
+                                   (4, 96, 96), (3, 160, 160), (2, 192, 192)],
                          ids=lambda s: "x".join(map(str, s)))
 def test_plane_form_every_cluster_size_and_autotune(cuda_lib, shape):
     """Every instantiated cluster size of a plane shape (set through
@@ -237,7 +238,7 @@ def test_plane_form_every_cluster_size_and_autotune(cuda_lib, shape):
     Xo = oracle.r2c3d(x32.astype(np.float64))
     yo = oracle.c2r3d(Y.astype(np.complex128), n2)
     sizes = []
-    for C in (0, 1, 2, 4, 8, 16):
+    for C in (0, 1, 2, 3, 4, 5, 8, 16):
         plan = lib.Plan(n0, n1, n2)
         st = lib.fft3d_set_plane_choice(plan.handle, C)
         if st != lib.FFT3D_OK:
