@@ -1,0 +1,55 @@
+"""bench.py's host-side logic, on CPU: the byte model, the DRAM-traffic
+lookup, and the reference arm's JSON line (the FP64 oracle on host cores)."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_two_pass_bytes_model():
+    nbytes, N, M = bench.two_pass_bytes(512, 512, 512)
+    assert N == 512 ** 3 and M == 512 * 512 * 257
+    assert nbytes == 2 * (4 * N + 24 * M) == 4307550208
+
+
+def test_traffic_lookup_keys_on_pass_shape_and_sources():
+    src = bench.kernel_source_hash()
+    lines = [ln for ln in open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) if ln.startswith("pass=")]
+    assert lines, "the traffic table must list the captured passes"
+    kv = dict(tok.split("=", 1) for tok in lines[0].split() if "=" in tok)
+    got = bench.traffic_from_profile(kv["pass"], kv["shape"])
+    if kv["src"] == src:
+        assert got == float(kv["bytes_per_launch"])
+    else:
+        assert got is None  # sources changed since the capture: no traffic claimed
+    assert bench.traffic_from_profile(kv["pass"], "7x7x7") is None
+
+
+def _run(args, env=None):
+    e = dict(os.environ)
+    e.update(env or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, capture_output=True, text=True,
+                          env=e, timeout=600)
+
+
+def test_reference_arm_prints_one_json_line():
+    r = _run(["--impl", "reference", "--n", "16", "--steps", "2", "--warmup", "1"])
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "GB/s" and d["value"] > 0
+    assert d["higher_is_better"] is True and d["dtype"] == "f64"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_do_no_work():
+    r = _run(["--impl", "reference", "--n", "16", "--steps", "1"], env={"RANK": "1", "WORLD_SIZE": "2",
+                                                                          "LOCAL_RANK": "1"})
+    assert r.returncode == 0 and r.stdout.strip() == ""
