@@ -49,7 +49,7 @@ cudaError_t scratch_for_current_device(double** out)
 extern "C" int fft3d_energy_noalloc(const void* spec, int n0, int n1, int n2, int batch, double* total,
                                     double* shells, int nbins, void* stream)
 {
-    if (!spec || n0 < 1 || n1 < 1 || n2 < 2 || (n2 & 1) || batch < 1 || nbins < 1 || nbins > 8192 ||
+    if (!spec || n0 < 1 || n1 < 1 || n2 < 2 || batch < 1 || nbins < 1 || nbins > 8192 ||
         (!total && !shells))
         return FFT3D_ERR_INVALID_ARG;
     if (((uintptr_t)spec & 15) || ((uintptr_t)total & 7) || ((uintptr_t)shells & 7)) return FFT3D_ERR_MISALIGNED;

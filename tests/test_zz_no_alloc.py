@@ -38,7 +38,8 @@ def _noalloc(lib, spec, n0, n1, n2, batch, nbins):
 
 def test_noalloc_energy_matches_plan_energy_on_two_calls(cuda_lib):
     lib = cuda_lib
-    cases = [((64, 48, 40), 2, 30, 81), ((32, 32, 32), 1, 28, 83)]  # two calls in a row, different inputs
+    # two calls in a row, different inputs; then an odd n2 (no Nyquist bin)
+    cases = [((64, 48, 40), 2, 30, 81), ((32, 32, 32), 1, 28, 83), ((12, 10, 15), 1, 9, 85)]
     for (n0, n1, n2), batch, nbins, seed in cases:
         spec = _spectrum((n0, n1, n2 // 2 + 1), batch, seed)
         plan = lib.Plan(n0, n1, n2, batch=batch)
