@@ -582,10 +582,12 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
             }
         }
     }
-    // default n0-pass kernel: where the plain kernel takes wider column tiles
-    // than the TMA kernel (long axes), its longer row segments win at the n0
-    // stride (measured at n0 = 1024: 2.0 ms plain 16-wide vs 3.0 ms TMA 8-wide)
-    if (p->ax0.spec && p->ax0.spec->tma_W && p->ax0.spec->col_W > p->ax0.spec->tma_W) p->choice_tma = 0;
+    // default n0-pass kernel: the plain kernel for long n0 axes, whose rows lie
+    // megabytes apart (GB300: n0 = 1024, 16-wide 4.2 TB/s vs TMA 8-wide 2.9;
+    // n0 = 1536, 8-wide 2.9 vs 2.5; n0 = 2048, 8-wide 3.0 vs TMA 4-wide 1.3),
+    // and wherever its column tiles are wider than the TMA kernel's
+    if (p->ax0.spec && p->ax0.spec->tma_W && (p->ax0.spec->col_W > p->ax0.spec->tma_W || p->ax0.L >= 1024))
+        p->choice_tma = 0;
     if (dtype != FFT3D_F32) {
         if (!p->ax0.tc && !p->ax1.tc) {  // no axis with a tensor-core kernel: the form does not exist here
             free_plan(p);

@@ -532,6 +532,7 @@ __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constan
     constexpr int NBOX = ROWS_IN_MAP / BOXR;
     static_assert(ROWS_IN_MAP % BOXR == 0, "tile rows must split into boxes of <= 256 rows");
     static_assert(!PAIR || (L % 2 == 0 && W % 2 == 0), "row pairs need even L and W");
+    static_assert(STAGES >= 2, "one slot is consumed while the next is in flight: at least two slots");
     constexpr int WS = PAIR ? W + 2 : W;  // slot row width (complex values)
     constexpr unsigned TILE_BYTES = (unsigned)L * WS * sizeof(float2);
     constexpr size_t XBYTES = XB ? (size_t)L * W * sizeof(float2) : 0;

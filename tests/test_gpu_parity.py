@@ -129,6 +129,8 @@ SHAPES = [
     (6, 512, 60), (3, 256, 40), (4, 1024, 30), (5, 256, 512), (1536, 4, 12),
     # row pairs whose last column tile would hold one column
     (2, 512, 64), (3, 1024, 32), (2, 512, 512),
+    # n1 = 2048 through the 4-wide TMA kernel: row pairs (H = 17, ragged), plain rows (H = 16)
+    (2, 2048, 32), (2, 2048, 30),
     # a factor 7 on every axis (runtime-radix kernels, radix-7 codelet)
     (14, 28, 56), (7, 7, 14), (49, 6, 28), (112, 3, 98), (5, 21, 70),
     # odd n2 (full-length row transforms, no Nyquist bin)
@@ -705,6 +707,30 @@ def test_autotune_keeps_parity_and_choices_roundtrip(cuda_lib):
         plan.c2r(Y.data_ptr(), y.data_ptr())
         assert rel_l2(y.cpu().numpy() / (n0 * n1 * n2), x32.astype(np.float64)) <= TOL_RT
     assert lib.fft3d_set_choices(plan.handle, [0, 0, 0, 2, 0]) == lib.FFT3D_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("shape", [(2048, 2, 6), (1536, 4, 12), (2, 2048, 32), (2, 2048, 30)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_long_axis_column_forms_match_oracle(cuda_lib, shape):
+    """Every column-kernel form of the 1536- and 2048-long axes (the TMA ring,
+    plain or row pairs; the plain kernel at full and half width) gives the
+    oracle's transform, forward and back."""
+    lib = cuda_lib
+    n0, n1, n2 = shape
+    plan = lib.Plan(n0, n1, n2)
+    x32 = synth.uniform_field(shape, seed=57).astype(np.float32)
+    ref = oracle.r2c3d(x32.astype(np.float64))
+    xd = torch.from_numpy(x32).cuda()
+    X = torch.empty((n0, n1, n2 // 2 + 1), dtype=torch.complex64, device="cuda")
+    for choice in ([0, 0, 0, 1, 1], [4, 4, 0, 0, 0], [0, 0, 0, 0, 0]):
+        assert lib.fft3d_set_choices(plan.handle, choice) == lib.FFT3D_OK
+        plan.r2c(xd.data_ptr(), X.data_ptr())
+        assert rel_l2(X.cpu().numpy(), ref) <= TOL, choice
+        Y = X.clone()
+        y = torch.empty_like(xd)
+        plan.c2r(Y.data_ptr(), y.data_ptr())
+        assert rel_l2(y.cpu().numpy() / (n0 * n1 * n2), x32.astype(np.float64)) <= TOL_RT, choice
+    plan.close()
 
 
 def test_tuned_plan_uses_the_cache(cuda_lib, tmp_path):
