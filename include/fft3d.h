@@ -60,7 +60,7 @@ typedef enum {
 typedef enum {
     FFT3D_OK = 0,
     FFT3D_ERR_INVALID_ARG = 1,      /* NULL/overlapping pointers, bad enum, n < 1, batch < 1 */
-    FFT3D_ERR_UNSUPPORTED_SIZE = 2, /* a prime factor other than 2, 3, 5, 7, or too long an axis */
+    FFT3D_ERR_UNSUPPORTED_SIZE = 2, /* an axis or row transform longer than 4096, or a form not offered at this size */
     FFT3D_ERR_MISALIGNED = 3,       /* a data pointer not 16-byte aligned */
     FFT3D_ERR_ALLOC = 4,            /* plan-time device allocation failed */
     FFT3D_ERR_CUDA = 5,             /* a CUDA call or launch failed */
@@ -97,14 +97,17 @@ typedef enum {
 
 /*
  * Create a plan for batch transforms of size n0 x n1 x n2 (Sec. 2).
- * Requirements: n0, n1 >= 1, n2 >= 2, every prime factor of n0, n1 and of the
- * row transform length (n2/2 for even n2, n2 for odd n2) in {2, 3, 5, 7}
- * (lengths with a factor 7, and odd n2, run the runtime-radix kernels), no
- * transform longer than 4096, H = floor(n2/2) + 1 (no Nyquist bin for odd n2),
- * batch >= 1, and a current CUDA device.  Chooses the passes and the kernel
- * shapes, computes twiddle tables in FP64 on the host, rounds them to FP32 and
- * copies them to the device.  Blocks.  Returns NULL on error (reason in
- * fft3d_last_error()).
+ * Requirements: n0, n1 >= 1, n2 >= 2, no transform longer than 4096 (n0, n1
+ * and the row transform length: n2/2 for even n2, n2 for odd n2),
+ * H = floor(n2/2) + 1 (no Nyquist bin for odd n2), batch >= 1, and a current
+ * CUDA device.  Lengths with compile-time kernels run those; other lengths whose
+ * prime factors are 2, 3, 5 and 7 (and odd n2) run the runtime-radix kernels;
+ * a length with any larger prime factor runs Bluestein's chirp-z form (two
+ * power-of-two transforms of length M >= 2L - 1 around a pointwise product; its
+ * chirp tables are computed in FP64 and take (L + 2M) x 8 bytes of device
+ * memory).  Chooses the passes and the kernel shapes, computes twiddle tables in
+ * FP64 on the host, rounds them to FP32 and copies them to the device.  Blocks.
+ * Returns NULL on error (reason in fft3d_last_error()).
  */
 fft3d_handle fft3d_plan(int n0, int n1, int n2, int dtype, int batch);
 

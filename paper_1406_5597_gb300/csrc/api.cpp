@@ -13,8 +13,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -112,10 +114,13 @@ std::vector<float2> forward_table(long long L, long long count)
     return t;
 }
 
+// Stockham radices of a 2357-smooth length; no stages (nst = 0) for any other
+// length, which runs in Bluestein form (setup_bluestein).
 GenPlan generic_radices(int L)
 {
     GenPlan g{};
     g.L = L;
+    if (!smooth2357(L)) return g;
     int rem = L;
     while (rem > 1) {
         int R = 0;
@@ -133,7 +138,86 @@ struct Axis {
     const TcEntry* tc = nullptr;  // tensor-core radix-16 column kernel (TC dtypes)
     GenPlan gen{};
     float2* d_tw = nullptr;
+    float2* d_blu = nullptr;  // Bluestein tables (chirp, bhat, W_M), lengths with a prime factor above 7
 };
+
+cudaError_t upload(const std::vector<float2>& h, float2** d);
+
+int next_pow2(int n)
+{
+    int m = 1;
+    while (m < n) m <<= 1;
+    return m;
+}
+
+// In-place forward (negative-sign) FFT of a power-of-two length in FP64:
+// bit-reversal permutation, then radix-2 butterflies of growing span.
+void fft_pow2_fp64(std::vector<double>& re, std::vector<double>& im)
+{
+    const int n = (int)re.size();
+    for (int i = 1, j = 0; i < n; ++i) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            std::swap(re[i], re[j]);
+            std::swap(im[i], im[j]);
+        }
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        const int half = len / 2;
+        for (int k = 0; k < half; ++k) {
+            double c, s;
+            root_of_unity(k, len, &c, &s);
+            const double wr = c, wi = -s;  // W_len^k = exp(-2 pi i k / len)
+            for (int i = k; i < n; i += len) {
+                const int j = i + half;
+                const double tr = re[j] * wr - im[j] * wi, ti = re[j] * wi + im[j] * wr;
+                re[j] = re[i] - tr;
+                im[j] = im[i] - ti;
+                re[i] += tr;
+                im[i] += ti;
+            }
+        }
+    }
+}
+
+// Bluestein form of a length-L axis (L has a prime factor above 7): M is the
+// smallest power of two >= 2L - 1, and one device array holds, rounded to FP32
+// from FP64, the chirp c[n] = exp(-i pi n^2 / L) (n^2 reduced mod 2L, so the
+// angle is exact), bhat = (1/M) FFT_M(b) with b[m] = b[M - m] = conj(c[m]) for
+// m < L (zero elsewhere), and the length-M forward table.
+cudaError_t setup_bluestein(Axis& a)
+{
+    const int L = a.L, M = next_pow2(2 * L - 1);
+    const GenPlan mg = generic_radices(M);
+    a.gen.M = M;
+    a.gen.mst = mg.nst;
+    std::memcpy(a.gen.mradix, mg.radix, sizeof mg.radix);
+    std::vector<float2> h((size_t)L + 2 * (size_t)M);
+    std::vector<double> br((size_t)M, 0.0), bi((size_t)M, 0.0);
+    for (long long n = 0; n < L; ++n) {
+        double c, s;
+        root_of_unity((n * n) % (2LL * L), 2LL * L, &c, &s);  // exp(+i pi n^2 / L) = conj(c[n])
+        h[(size_t)n] = make_float2((float)c, (float)(-s));
+        br[(size_t)n] = c;
+        bi[(size_t)n] = s;
+        if (n > 0) {
+            br[(size_t)(M - n)] = c;
+            bi[(size_t)(M - n)] = s;
+        }
+    }
+    fft_pow2_fp64(br, bi);
+    for (int k = 0; k < M; ++k) h[(size_t)L + k] = make_float2((float)(br[k] / M), (float)(bi[k] / M));
+    const std::vector<float2> tw = forward_table(M, M);
+    std::copy(tw.begin(), tw.end(), h.begin() + L + M);
+    const cudaError_t e = upload(h, &a.d_blu);
+    if (e != cudaSuccess) return e;
+    a.gen.chirp = a.d_blu;
+    a.gen.bhat = a.d_blu + L;
+    a.gen.twm = a.d_blu + L + M;
+    return cudaSuccess;
+}
 
 const TcEntry* find_tc(int L)
 {
@@ -240,9 +324,10 @@ void free_plan(fft3d_plan_s* p)
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
-    cudaFree(p->ax0.d_tw);
-    cudaFree(p->ax1.d_tw);
-    cudaFree(p->ax2.d_tw);
+    for (Axis* a : {&p->ax0, &p->ax1, &p->ax2}) {
+        cudaFree(a->d_tw);
+        cudaFree(a->d_blu);
+    }
     cudaFree(p->d_twpack);
     cudaFree(p->d_status);
     cudaFree(p->d_counters);
@@ -379,7 +464,10 @@ std::string axis_desc(const fft3d_plan_s* p, const Axis& a, bool row)
         return b;
     }
     if (uses_generic(p, a, row)) {
-        std::snprintf(b, sizeof b, "generic L=%d", a.L);
+        if (a.gen.M)
+            std::snprintf(b, sizeof b, "generic L=%d bluestein M=%d", a.L, a.gen.M);
+        else
+            std::snprintf(b, sizeof b, "generic L=%d", a.L);
     } else if (row) {
         const int rr = (p->choice_rows > 0 && p->choice_rows <= a.spec->row_rows && a.spec->row_warp)
                            ? p->choice_rows
@@ -509,7 +597,7 @@ const char* fft3d_error_string(int status)
     switch (status) {
     case FFT3D_OK: return "ok";
     case FFT3D_ERR_INVALID_ARG: return "invalid argument";
-    case FFT3D_ERR_UNSUPPORTED_SIZE: return "unsupported size (n0, n1 and n2/2 (n2 for odd n2) must be 2,3,5,7-smooth and <= 4096)";
+    case FFT3D_ERR_UNSUPPORTED_SIZE: return "unsupported size (n0, n1 and n2/2 (n2 for odd n2) must be <= 4096) or form not offered at this size";
     case FFT3D_ERR_MISALIGNED: return "data pointer not 16-byte aligned";
     case FFT3D_ERR_ALLOC: return "device allocation failed";
     case FFT3D_ERR_CUDA: return "CUDA error";
@@ -536,8 +624,7 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
     }
     // the row transform has length n2/2 (even n2, half-length packing) or n2 (odd n2)
     const int row_len = (n2 & 1) ? n2 : n2 / 2;
-    if (!smooth2357(n0) || !smooth2357(n1) || !smooth2357(row_len) || n0 > kMaxAxis || n1 > kMaxAxis ||
-        row_len > kMaxAxis) {
+    if (n0 < 1 || n1 < 1 || row_len < 1 || n0 > kMaxAxis || n1 > kMaxAxis || row_len > kMaxAxis) {
         fail(FFT3D_ERR_UNSUPPORTED_SIZE);
         return nullptr;
     }
@@ -574,12 +661,11 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
         a.spec = (i == 2 && (n2 & 1)) ? nullptr : find_len(a.L);  // odd rows: the runtime-length kernel
         a.tc = (dtype != FFT3D_F32 && i < 2) ? find_tc(a.L) : nullptr;
         a.gen = generic_radices(a.L);
-        if (a.L >= 1) {
-            if (upload(forward_table(a.L, a.L), &a.d_tw) != cudaSuccess) {
-                free_plan(p);
-                fail(FFT3D_ERR_ALLOC);
-                return nullptr;
-            }
+        if (upload(forward_table(a.L, a.L), &a.d_tw) != cudaSuccess ||
+            (!smooth2357(a.L) && setup_bluestein(a) != cudaSuccess)) {
+            free_plan(p);
+            fail(FFT3D_ERR_ALLOC);
+            return nullptr;
         }
     }
     // default n0-pass kernel: the plain kernel for long n0 axes, whose rows lie

@@ -44,12 +44,30 @@ struct RowArgs {
                            // rows of 2H floats); in floats for odd n2 (n2 dense, 2H = n2 + 1 padded)
 };
 
-// Runtime radix plan for the generic (any 2/3/5-smooth length) kernels.
+// Runtime plan for the generic (any length) kernels.  A length whose prime
+// factors are 2, 3, 5 and 7 runs its Stockham stages directly (radix list).
+// Any other length runs Bluestein's chirp-z form (M > 0): with
+// c[n] = exp(-i pi n^2 / L), the DFT is X[k] = c[k] sum_n (x[n] c[n]) conj(c[k - n]),
+// a cyclic convolution of length M (a power of two >= 2L - 1) done by two
+// length-M transforms and a pointwise product with the transformed chirp.
 struct GenPlan {
     int L;
     int nst;
     int radix[24];
+    int M;                // 0: direct stages; else the convolution length
+    int mst;              // stages of the length-M transforms
+    int mradix[24];
+    const float2* chirp;  // c[n], n < L (device)
+    const float2* bhat;   // (1/M) FFT_M of b, b[m] = b[M - m] = conj(c[m]) for m < L, else 0 (device)
+    const float2* twm;    // W_M^x = exp(-2 pi i x / M), x < M (device)
 };
+
+// Slots per line of a generic kernel's shared buffers: the L + 1 bins of an
+// unpacked row, or the M points of a Bluestein convolution.
+__host__ __device__ inline int gen_line_slots(const GenPlan& g)
+{
+    return g.M > g.L + 1 ? g.M : g.L + 1;
+}
 
 // Launchers take a runtime shape choice: w = columns per CTA (0 or > compiled
 // maximum: the compiled value), rows = rows per CTA (same rule).

@@ -226,20 +226,4 @@ struct Dft<32, DIR> {
     __device__ __forceinline__ static void run(float2* a) { DftSplit<4, 8, DIR>::run(a); }
 };
 
-// Runtime radix dispatch for the generic kernels.
-template <int DIR>
-__device__ __forceinline__ void dft_runtime(int R, float2* a)
-{
-    switch (R) {
-    case 2: Dft<2, DIR>::run(a); break;
-    case 3: Dft<3, DIR>::run(a); break;
-    case 4: Dft<4, DIR>::run(a); break;
-    case 5: Dft<5, DIR>::run(a); break;
-    case 7: Dft<7, DIR>::run(a); break;
-    case 8: Dft<8, DIR>::run(a); break;
-    case 16: Dft<16, DIR>::run(a); break;
-    default: break;
-    }
-}
-
 }  // namespace fft3d

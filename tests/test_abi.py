@@ -30,9 +30,9 @@ def test_error_strings(lib):
 @pytest.mark.parametrize("dims,status", [
     ((0, 8, 8), fft3d.FFT3D_ERR_INVALID_ARG),
     ((8, 8, 1), fft3d.FFT3D_ERR_INVALID_ARG),
-    ((8, 8, 11), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),  # odd n2 with a factor 11
-    ((22, 8, 8), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),  # factor 11
-    ((8, 8, 22), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),  # n2/2 = 11
+    ((8, 8, 8193), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),  # odd row longer than 4096
+    ((4097, 8, 8), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),  # prime axis beyond 4096
+    ((8, 8, 8194), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),  # n2/2 = 4097
     ((8192, 8, 8), fft3d.FFT3D_ERR_UNSUPPORTED_SIZE),
 ])
 def test_plan_rejects_bad_sizes_before_touching_the_device(lib, dims, status):
@@ -53,7 +53,7 @@ def test_plan_rejects_bad_dtype_batch_flags(lib):
 
 
 def test_nonlinear_plan_rejects_bad_sizes(lib):
-    assert not fft3d.fft3d_nonlinear_plan(8, 8, 11)
+    assert not fft3d.fft3d_nonlinear_plan(8, 8, 8194)
     assert fft3d.fft3d_last_error() == fft3d.FFT3D_ERR_UNSUPPORTED_SIZE
     assert fft3d.fft3d_nonlinear_exec(None, 16, 32) == fft3d.FFT3D_ERR_INVALID_ARG
     assert fft3d.fft3d_nonlinear_workspace_bytes(None) == 0

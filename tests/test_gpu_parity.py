@@ -133,6 +133,10 @@ SHAPES = [
     (2, 2048, 32), (2, 2048, 30),
     # a factor 7 on every axis (runtime-radix kernels, radix-7 codelet)
     (14, 28, 56), (7, 7, 14), (49, 6, 28), (112, 3, 98), (5, 21, 70),
+    # prime factors above 7 (Bluestein form): every axis, odd and even n2, ragged
+    # column tiles, and the longest prime lengths (M = 8192)
+    (11, 13, 22), (17, 4, 26), (6, 97, 8), (4, 6, 13), (3, 1021, 4), (143, 3, 10), (2, 2, 8186), (4093, 2, 3),
+    (2, 4093, 2), (3, 2, 4093),
     # odd n2 (full-length row transforms, no Nyquist bin)
     (8, 6, 15), (4, 10, 9), (5, 3, 21), (16, 16, 45), (3, 7, 35), (6, 4, 3), (32, 32, 27), (2, 2, 875),
 ]
@@ -268,7 +272,7 @@ def test_plane_form_every_cluster_size_and_autotune(cuda_lib, shape):
 
 
 PADDED_SHAPES = [(32, 32, 32), (64, 64, 64), (6, 512, 60), (8, 6, 1024), (3, 2, 2048), (2, 3, 4096), (48, 80, 96),
-                 (5, 3, 2), (1, 8, 16), (4, 6, 9), (3, 5, 15)]
+                 (5, 3, 2), (1, 8, 16), (4, 6, 9), (3, 5, 15), (4, 6, 26), (3, 11, 13)]
 
 
 @pytest.mark.parametrize("extra", ["plain", "generic", "tc"])
@@ -533,7 +537,8 @@ def test_argument_errors_leave_output_untouched(cuda_lib):
 TOL_NL = 1e-5
 
 
-@pytest.mark.parametrize("shape", [(32, 32, 32), (32, 48, 64), (256, 256, 256)], ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("shape", [(32, 32, 32), (32, 48, 64), (256, 256, 256), (22, 13, 32)],
+                         ids=lambda s: "x".join(map(str, s)))
 def test_nonlinear_term_matches_oracle(cuda_lib, shape):
     n0, n1, n2 = shape
     U = synth.spectral_velocity(n0, n1, n2, seed=synth.seed_for_config(4))
@@ -615,7 +620,7 @@ def gpu_c2r_dtype(lib, Y64, n2, dtype):
 
 @pytest.mark.parametrize("dtype", [1, 2], ids=["bf16x3", "fp16"])
 @pytest.mark.parametrize("shape", [(256, 256, 32), (512, 64, 16), (32, 512, 16), (1024, 16, 8), (2048, 4, 6),
-                                   (256, 24, 20)], ids=lambda s: "x".join(map(str, s)) if isinstance(s, tuple) else s)
+                                   (256, 24, 20), (256, 11, 26)], ids=lambda s: "x".join(map(str, s)) if isinstance(s, tuple) else s)
 def test_tensor_core_forms_match_oracle(cuda_lib, shape, dtype):
     n0, n1, n2 = shape
     x32 = synth.uniform_field(shape, seed=101).astype(np.float32)

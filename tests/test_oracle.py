@@ -29,7 +29,9 @@ def rel_l2(a, b):
 TINY = [(n0, n1, n2) for n0, n1, n2 in itertools.product((2, 3, 4, 5, 6, 8, 10), (2, 3, 5, 6, 12),
                                                          (2, 4, 6, 10, 16))
         if n0 * n1 * n2 <= 8192][::3] + [(6, 10, 16), (8, 8, 8), (15, 12, 10), (16, 16, 16), (7, 6, 14), (14, 7, 4),
-                                          (4, 6, 9), (5, 3, 15), (6, 8, 7), (3, 5, 3), (2, 2, 21)]
+                                          (4, 6, 9), (5, 3, 15), (6, 8, 7), (3, 5, 3), (2, 2, 21),
+                                          # prime factors above 7 on every axis (the direct-sum branch)
+                                          (11, 2, 4), (2, 13, 6), (3, 2, 22), (2, 3, 26), (4, 2, 13), (2, 2, 34)]
 
 
 @pytest.mark.parametrize("shape", TINY)
@@ -59,7 +61,7 @@ def test_textbook_dft4():
     assert np.max(np.abs(got - expect)) < 1e-14
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 12, 30, 49, 64, 96, 160, 210, 512])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 12, 30, 49, 64, 96, 160, 210, 512, 11, 13, 26, 97, 143, 1021, 4093])
 def test_fft1d_matches_numpy(n):
     rng = np.random.default_rng(n)
     x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
@@ -68,7 +70,7 @@ def test_fft1d_matches_numpy(n):
 
 
 @pytest.mark.parametrize("shape", [(32, 32, 32), (6, 10, 16), (15, 12, 10), (64, 48, 40), (2, 2, 2), (16, 12, 45),
-                                   (8, 10, 27)])
+                                   (8, 10, 27), (11, 13, 34), (17, 6, 26), (6, 97, 13)])
 def test_r2c_matches_numpy_rfftn(shape):
     x = synth.uniform_field(shape, seed=3)
     assert rel_l2(oracle.r2c3d(x), np.fft.rfftn(x)) < 1e-13
