@@ -381,6 +381,29 @@ def main():
         variants["preserve_input"] = {"ms_per_step": vms, "gbs_effective": nbytes / (vms * 1e-3) / 1e9,
                                       "slowdown_vs_transpose_free": vms / ms, "plan": vp.describe()}
         vp.close()
+        # the FP64 path (FFT3D_F64: double data, runtime-length kernels); its
+        # minimum bytes are twice the FP32 step's
+        vp = fft3d.Plan(n0, n1, n2, dtype=fft3d.FFT3D_F64)
+        x64 = x.double()
+        X64 = torch.empty((n0, n1, H), dtype=torch.complex128, device=dev)
+        y64 = torch.empty_like(x64)
+
+        def dstep(vp=vp):
+            vp.r2c(x64.data_ptr(), X64.data_ptr(), sptr)
+            vp.c2r(X64.data_ptr(), y64.data_ptr(), sptr)
+
+        for _ in range(3):
+            dstep()
+        vms = time_steps(dstep, stream, max(5, args.steps // 2)) / max(5, args.steps // 2)
+        vp.r2c(x64.data_ptr(), X64.data_ptr(), sptr)
+        vp.c2r(X64.data_ptr(), y64.data_ptr(), sptr)
+        torch.cuda.synchronize(dev)
+        rt = float((y64 / (n0 * n1 * n2) - x64).norm() / x64.norm())
+        variants["fp64"] = {"ms_per_step": vms, "gbs_effective": 2 * nbytes / (vms * 1e-3) / 1e9,
+                            "slowdown_vs_transpose_free": vms / ms, "round_trip_rel_l2": rt,
+                            "plan": vp.describe()}
+        vp.close()
+        del x64, X64, y64
         line["variants"] = variants
 
     # tensor-core radix-16 forms (split-BF16 x3, FP16) of the same step, with

@@ -50,11 +50,13 @@ extern "C" {
 
 typedef struct fft3d_plan_s* fft3d_handle;
 
-/* Arithmetic forms.  Storage is FP32 in every form. */
+/* Arithmetic forms.  Storage is FP32 in the first three (fft3d_r2c / fft3d_c2r)
+ * and FP64 in the last (fft3d_r2c_f64 / fft3d_c2r_f64). */
 typedef enum {
     FFT3D_F32 = 0,            /* plain FP32 butterflies on the CUDA cores */
     FFT3D_F32_TC_BF16X3 = 1,  /* radix-16 stages as tensor-core contractions, split-BF16 (3 products) */
-    FFT3D_F32_TC_F16 = 2      /* radix-16 stages as tensor-core contractions, single-term FP16 */
+    FFT3D_F32_TC_F16 = 2,     /* radix-16 stages as tensor-core contractions, single-term FP16 */
+    FFT3D_F64 = 3             /* FP64 data and arithmetic, runtime-length kernels (flags must be 0) */
 } fft3d_dtype;
 
 typedef enum {
@@ -143,6 +145,24 @@ int fft3d_r2c(fft3d_handle plan, const float* in, void* out, void* stream);
  */
 int fft3d_c2r(fft3d_handle plan, void* in, float* out, void* stream);
 
+/*
+ * FP64 forward r2c and inverse c2r, for FFT3D_F64 plans only (other plans, and
+ * FFT3D_F64 plans passed to fft3d_r2c / fft3d_c2r, give FFT3D_ERR_INVALID_ARG).
+ * Same transforms, pass sequence and layouts as fft3d_r2c / fft3d_c2r with
+ * flags 0, in double precision: every pass runs the runtime-length kernels
+ * (Stockham stages of radix 2..8, Bluestein for other primes) with twiddle and
+ * chirp tables computed and kept in FP64.  An FFT3D_F64 plan accepts lengths up
+ * to 4096, except that a length with a prime factor above 7 must be <= 2048 (its
+ * Bluestein line of 4096 double2 points fills one CTA's shared memory).
+ * r2c  in:  batch*n0*n1*n2 doubles (device), read only.
+ *      out: batch*n0*n1*H double2 (interleaved re, im; device), must not overlap in.
+ * c2r  in:  batch*n0*n1*H double2 (device), CLOBBERED (scratch, as in fft3d_c2r).
+ *      out: batch*n0*n1*n2 doubles (device), must not overlap in.  Unnormalised.
+ * Both pointers 16-byte aligned.  Asynchronous on stream.
+ */
+int fft3d_r2c_f64(fft3d_handle plan, const double* in, void* out, void* stream);
+int fft3d_c2r_f64(fft3d_handle plan, void* in, double* out, void* stream);
+
 /* Release a plan's device tables.  NULL-safe.  Blocks on the device. */
 void fft3d_destroy(fft3d_handle plan);
 
@@ -207,6 +227,7 @@ double fft3d_pass_bytes(fft3d_handle plan, int pass);
  * choices are five ints {w0, w1, rows, tma0, tma1} (widths/rows 0 = compiled
  * default; tma flags 0/1) that fft3d_get_choices / fft3d_set_choices read and
  * write (host array), so a caller can cache them per GPU and shape.
+ * FFT3D_F64 plans have nothing to tune: FFT3D_ERR_INVALID_ARG.
  */
 int fft3d_autotune(fft3d_handle plan, float* real, void* cplx, int reps, void* stream);
 int fft3d_get_choices(fft3d_handle plan, int* choices5);
@@ -240,6 +261,7 @@ int fft3d_set_plane_choice(fft3d_handle plan, int cluster);
  * and replayed with a single graph launch.  fft3d_group_plan_at gives group i's
  * plan (for fft3d_autotune / fft3d_set_choices; tune before the first call
  * with a given operand set, since a captured graph keeps the launch shapes).
+ * dtype FFT3D_F64 is not offered (FFT3D_ERR_INVALID_ARG).
  */
 typedef struct fft3d_group_s* fft3d_group_handle;
 fft3d_group_handle fft3d_plan_group(const int* dims, const int* counts, int ngroups, int dtype);
@@ -342,6 +364,7 @@ void fft3d_ns_destroy(fft3d_ns_handle ns);
  * a fixed order (deterministic).  Uses plan-owned scratch (allocated at plan
  * time for nbins up to the largest shell of the shape; a larger nbins grows
  * it, which synchronises the device).  Asynchronous on stream otherwise.
+ * FFT3D_F64 plans: FFT3D_ERR_INVALID_ARG (the spectra here are float2).
  */
 int fft3d_energy(fft3d_handle plan, const void* spec, double* total, double* shells, int nbins, void* stream);
 

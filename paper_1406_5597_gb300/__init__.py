@@ -23,6 +23,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "fft3d.h")
 FFT3D_F32 = 0
 FFT3D_F32_TC_BF16X3 = 1
 FFT3D_F32_TC_F16 = 2
+FFT3D_F64 = 3
 
 FFT3D_OK = 0
 FFT3D_ERR_INVALID_ARG = 1
@@ -53,6 +54,8 @@ _SIGS = {
     "fft3d_plan_variant": ([_I, _I, _I, _I, _I, _I], _P),
     "fft3d_r2c": ([_P, _P, _P, _P], _I),
     "fft3d_c2r": ([_P, _P, _P, _P], _I),
+    "fft3d_r2c_f64": ([_P, _P, _P, _P], _I),
+    "fft3d_c2r_f64": ([_P, _P, _P, _P], _I),
     "fft3d_destroy": ([_P], None),
     "fft3d_last_error": ([], _I),
     "fft3d_error_string": ([_I], ctypes.c_char_p),
@@ -148,6 +151,14 @@ def fft3d_r2c(plan, in_ptr, out_ptr, stream=0):
 
 def fft3d_c2r(plan, in_ptr, out_ptr, stream=0):
     return load().fft3d_c2r(_v(plan), _v(in_ptr), _v(out_ptr), _v(stream))
+
+
+def fft3d_r2c_f64(plan, in_ptr, out_ptr, stream=0):
+    return load().fft3d_r2c_f64(_v(plan), _v(in_ptr), _v(out_ptr), _v(stream))
+
+
+def fft3d_c2r_f64(plan, in_ptr, out_ptr, stream=0):
+    return load().fft3d_c2r_f64(_v(plan), _v(in_ptr), _v(out_ptr), _v(stream))
 
 
 def fft3d_destroy(plan):
@@ -490,14 +501,18 @@ class Plan:
         return fft3d_describe(self.handle)
 
     def r2c(self, in_ptr, out_ptr, stream=0):
-        st = fft3d_r2c(self.handle, in_ptr, out_ptr, stream)
+        """Forward r2c through fft3d_r2c, or fft3d_r2c_f64 for an FFT3D_F64 plan."""
+        f64 = self.dtype == FFT3D_F64
+        st = (fft3d_r2c_f64 if f64 else fft3d_r2c)(self.handle, in_ptr, out_ptr, stream)
         if st != FFT3D_OK:
-            raise Fft3dError(st, "fft3d_r2c")
+            raise Fft3dError(st, "fft3d_r2c_f64" if f64 else "fft3d_r2c")
 
     def c2r(self, in_ptr, out_ptr, stream=0):
-        st = fft3d_c2r(self.handle, in_ptr, out_ptr, stream)
+        """Inverse c2r through fft3d_c2r, or fft3d_c2r_f64 for an FFT3D_F64 plan."""
+        f64 = self.dtype == FFT3D_F64
+        st = (fft3d_c2r_f64 if f64 else fft3d_c2r)(self.handle, in_ptr, out_ptr, stream)
         if st != FFT3D_OK:
-            raise Fft3dError(st, "fft3d_c2r")
+            raise Fft3dError(st, "fft3d_c2r_f64" if f64 else "fft3d_c2r")
 
     def energy(self, spec, nbins):
         """(total, shells) FP64 CUDA tensors of a complex64 CUDA spectrum tensor."""
@@ -542,14 +557,21 @@ def _stream_ptr(stream):
 
 def rfft3(x, dtype=FFT3D_F32, flags=0, stream=None):
     """Forward r2c of a float32 CUDA tensor (..., n0, n1, n2) -> complex64
-    (..., n0, n1, n2/2+1); leading dimensions form the batch."""
+    (..., n0, n1, n2/2+1); leading dimensions form the batch.  A float64
+    tensor runs the FP64 path (FFT3D_F64) into complex128."""
     import torch
-    if not (x.is_cuda and x.dtype == torch.float32):
-        raise TypeError("rfft3 needs a float32 CUDA tensor")
+    if not (x.is_cuda and x.dtype in (torch.float32, torch.float64)):
+        raise TypeError("rfft3 needs a float32 or float64 CUDA tensor")
+    f64 = x.dtype == torch.float64
+    if f64:
+        dtype = FFT3D_F64
+    elif dtype == FFT3D_F64:
+        raise TypeError("FFT3D_F64 needs a float64 tensor")
     x = x.contiguous()
     n0, n1, n2 = x.shape[-3:]
     batch = int(x.numel() // (n0 * n1 * n2)) if x.numel() else 0
-    out = torch.empty(x.shape[:-1] + (n2 // 2 + 1,), dtype=torch.complex64, device=x.device)
+    out = torch.empty(x.shape[:-1] + (n2 // 2 + 1,), dtype=torch.complex128 if f64 else torch.complex64,
+                      device=x.device)
     if batch == 0:
         return out
     _cached_plan((n0, n1, n2), batch, dtype, flags).r2c(x.data_ptr(), out.data_ptr(), _stream_ptr(stream))
@@ -557,17 +579,23 @@ def rfft3(x, dtype=FFT3D_F32, flags=0, stream=None):
 
 
 def irfft3(X, n2, dtype=FFT3D_F32, flags=0, inplace_ok=False, stream=None):
-    """Inverse c2r (unnormalised) of a complex64 CUDA tensor (..., n0, n1, n2/2+1).
-    The library clobbers its input, so X is cloned unless inplace_ok."""
+    """Inverse c2r (unnormalised) of a complex64 CUDA tensor (..., n0, n1, n2/2+1);
+    a complex128 tensor runs the FP64 path into float64.  The library clobbers
+    its input, so X is cloned unless inplace_ok."""
     import torch
-    if not (X.is_cuda and X.dtype == torch.complex64):
-        raise TypeError("irfft3 needs a complex64 CUDA tensor")
+    if not (X.is_cuda and X.dtype in (torch.complex64, torch.complex128)):
+        raise TypeError("irfft3 needs a complex64 or complex128 CUDA tensor")
+    f64 = X.dtype == torch.complex128
+    if f64:
+        dtype = FFT3D_F64
+    elif dtype == FFT3D_F64:
+        raise TypeError("FFT3D_F64 needs a complex128 tensor")
     n0, n1, H = X.shape[-3:]
     if H != n2 // 2 + 1:
         raise ValueError("last dimension must be n2/2+1")
     X = X.contiguous() if inplace_ok else X.clone(memory_format=torch.contiguous_format)
     batch = int(X.numel() // (n0 * n1 * H)) if X.numel() else 0
-    out = torch.empty(X.shape[:-1] + (n2,), dtype=torch.float32, device=X.device)
+    out = torch.empty(X.shape[:-1] + (n2,), dtype=torch.float64 if f64 else torch.float32, device=X.device)
     if batch == 0:
         return out
     _cached_plan((n0, n1, n2), batch, dtype, flags).c2r(X.data_ptr(), out.data_ptr(), _stream_ptr(stream))

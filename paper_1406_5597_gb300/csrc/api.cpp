@@ -139,7 +139,13 @@ struct Axis {
     GenPlan gen{};
     float2* d_tw = nullptr;
     float2* d_blu = nullptr;  // Bluestein tables (chirp, bhat, W_M), lengths with a prime factor above 7
+    // FFT3D_F64 plans: the same tables in FP64
+    GenPlan64 gen64{};
+    double2* d_tw64 = nullptr;
+    double2* d_blu64 = nullptr;
 };
+
+bool is_tc_dtype(int dtype) { return dtype == FFT3D_F32_TC_BF16X3 || dtype == FFT3D_F32_TC_F16; }
 
 cudaError_t upload(const std::vector<float2>& h, float2** d);
 
@@ -182,24 +188,50 @@ void fft_pow2_fp64(std::vector<double>& re, std::vector<double>& im)
     }
 }
 
+// Forward-sign table W_L^m, m in [0, count), in FP64.
+std::vector<double2> forward_table64(long long L, long long count)
+{
+    std::vector<double2> t((size_t)count);
+    for (long long m = 0; m < count; ++m) {
+        double c, s;
+        root_of_unity(m, L, &c, &s);
+        t[(size_t)m] = make_double2(c, -s);
+    }
+    return t;
+}
+
+cudaError_t upload64(const std::vector<double2>& h, double2** d)
+{
+    cudaError_t e = cudaMalloc((void**)d, h.size() * sizeof(double2));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*d, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice);
+}
+
+// The FP64 chirp, transformed chirp and length-M table of a Bluestein axis
+// (exactly as setup_bluestein, without the rounding to FP32).
+struct BluesteinTables {
+    int M;
+    std::vector<double2> chirp, bhat, tw;
+};
+BluesteinTables bluestein_tables(int L);
+
 // Bluestein form of a length-L axis (L has a prime factor above 7): M is the
 // smallest power of two >= 2L - 1, and one device array holds, rounded to FP32
 // from FP64, the chirp c[n] = exp(-i pi n^2 / L) (n^2 reduced mod 2L, so the
 // angle is exact), bhat = (1/M) FFT_M(b) with b[m] = b[M - m] = conj(c[m]) for
 // m < L (zero elsewhere), and the length-M forward table.
-cudaError_t setup_bluestein(Axis& a)
+BluesteinTables bluestein_tables(int L)
 {
-    const int L = a.L, M = next_pow2(2 * L - 1);
-    const GenPlan mg = generic_radices(M);
-    a.gen.M = M;
-    a.gen.mst = mg.nst;
-    std::memcpy(a.gen.mradix, mg.radix, sizeof mg.radix);
-    std::vector<float2> h((size_t)L + 2 * (size_t)M);
+    BluesteinTables t;
+    const int M = next_pow2(2 * L - 1);
+    t.M = M;
+    t.chirp.resize((size_t)L);
+    t.bhat.resize((size_t)M);
     std::vector<double> br((size_t)M, 0.0), bi((size_t)M, 0.0);
     for (long long n = 0; n < L; ++n) {
         double c, s;
         root_of_unity((n * n) % (2LL * L), 2LL * L, &c, &s);  // exp(+i pi n^2 / L) = conj(c[n])
-        h[(size_t)n] = make_float2((float)c, (float)(-s));
+        t.chirp[(size_t)n] = make_double2(c, -s);
         br[(size_t)n] = c;
         bi[(size_t)n] = s;
         if (n > 0) {
@@ -208,14 +240,59 @@ cudaError_t setup_bluestein(Axis& a)
         }
     }
     fft_pow2_fp64(br, bi);
-    for (int k = 0; k < M; ++k) h[(size_t)L + k] = make_float2((float)(br[k] / M), (float)(bi[k] / M));
-    const std::vector<float2> tw = forward_table(M, M);
-    std::copy(tw.begin(), tw.end(), h.begin() + L + M);
+    for (int k = 0; k < M; ++k) t.bhat[(size_t)k] = make_double2(br[k] / M, bi[k] / M);
+    t.tw = forward_table64(M, M);
+    return t;
+}
+
+cudaError_t setup_bluestein(Axis& a)
+{
+    const int L = a.L;
+    const BluesteinTables t = bluestein_tables(L);
+    const int M = t.M;
+    const GenPlan mg = generic_radices(M);
+    a.gen.M = M;
+    a.gen.mst = mg.nst;
+    std::memcpy(a.gen.mradix, mg.radix, sizeof mg.radix);
+    std::vector<float2> h((size_t)L + 2 * (size_t)M);
+    for (int n = 0; n < L; ++n) h[(size_t)n] = make_float2((float)t.chirp[n].x, (float)t.chirp[n].y);
+    for (int k = 0; k < M; ++k) {
+        h[(size_t)L + k] = make_float2((float)t.bhat[k].x, (float)t.bhat[k].y);
+        h[(size_t)L + M + k] = make_float2((float)t.tw[k].x, (float)t.tw[k].y);
+    }
     const cudaError_t e = upload(h, &a.d_blu);
     if (e != cudaSuccess) return e;
     a.gen.chirp = a.d_blu;
     a.gen.bhat = a.d_blu + L;
     a.gen.twm = a.d_blu + L + M;
+    return cudaSuccess;
+}
+
+// The FP64 plan of an axis: the radices of a.gen and FP64 tables (the axis
+// table, and for a Bluestein length the FP64 chirp tables).
+cudaError_t setup_axis64(Axis& a)
+{
+    a.gen64.L = a.gen.L;
+    a.gen64.nst = a.gen.nst;
+    std::memcpy(a.gen64.radix, a.gen.radix, sizeof a.gen.radix);
+    cudaError_t e = upload64(forward_table64(a.L, a.L), &a.d_tw64);
+    if (e != cudaSuccess || smooth2357(a.L)) return e;
+    const int L = a.L;
+    const BluesteinTables t = bluestein_tables(L);
+    const int M = t.M;
+    const GenPlan mg = generic_radices(M);
+    a.gen64.M = M;
+    a.gen64.mst = mg.nst;
+    std::memcpy(a.gen64.mradix, mg.radix, sizeof mg.radix);
+    std::vector<double2> h;
+    h.reserve((size_t)L + 2 * (size_t)M);
+    h.insert(h.end(), t.chirp.begin(), t.chirp.end());
+    h.insert(h.end(), t.bhat.begin(), t.bhat.end());
+    h.insert(h.end(), t.tw.begin(), t.tw.end());
+    if ((e = upload64(h, &a.d_blu64)) != cudaSuccess) return e;
+    a.gen64.chirp = a.d_blu64;
+    a.gen64.bhat = a.d_blu64 + L;
+    a.gen64.twm = a.d_blu64 + L + M;
     return cudaSuccess;
 }
 
@@ -280,6 +357,7 @@ struct fft3d_plan_s {
     int device = 0;
     Axis ax0, ax1, ax2;  // ax2: the row transform, length n2/2 (even n2) or n2 (odd n2)
     float2* d_twpack = nullptr;
+    double2* d_twpack64 = nullptr;  // FFT3D_F64 plans
     int* d_status = nullptr;
     const PlaneEntry* plane = nullptr;  // fused n2+n1 kernel, when one fits this shape
     const CPlaneEntry* cplane = nullptr;  // cluster (distributed shared memory) n2+n1 kernel
@@ -327,7 +405,10 @@ void free_plan(fft3d_plan_s* p)
     for (Axis* a : {&p->ax0, &p->ax1, &p->ax2}) {
         cudaFree(a->d_tw);
         cudaFree(a->d_blu);
+        cudaFree(a->d_tw64);
+        cudaFree(a->d_blu64);
     }
+    cudaFree(p->d_twpack64);
     cudaFree(p->d_twpack);
     cudaFree(p->d_status);
     cudaFree(p->d_counters);
@@ -572,6 +653,7 @@ std::string describe_plan(const fft3d_plan_s* p)
     }
     if (flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE)
         d += (flags & FFT3D_FLAG_TRANSPOSE_BACK) ? " explicit-transpose+back" : " explicit-transpose";
+    if (p->dtype == FFT3D_F64) d = "fp64 " + d;
     return d;
 }
 
@@ -611,7 +693,8 @@ int fft3d_last_error(void) { return g_last_error; }
 
 fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, int flags)
 {
-    if (n0 < 1 || n1 < 1 || n2 < 2 || batch < 1 || dtype < 0 || dtype > 2 ||
+    if (n0 < 1 || n1 < 1 || n2 < 2 || batch < 1 || dtype < 0 || dtype > FFT3D_F64 ||
+        (dtype == FFT3D_F64 && flags != 0) ||
         (flags & ~(FFT3D_FLAG_EXPLICIT_TRANSPOSE | FFT3D_FLAG_TRANSPOSE_BACK | FFT3D_FLAG_THREE_PASS |
                    FFT3D_FLAG_GENERIC | FFT3D_FLAG_TEST_SKIP_ARRIVAL | FFT3D_FLAG_FUSED_PLANE |
                    FFT3D_FLAG_CLUSTER_PLANE | FFT3D_FLAG_PADDED_REAL | FFT3D_FLAG_PRESERVE_INPUT)) ||
@@ -628,6 +711,13 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
         fail(FFT3D_ERR_UNSUPPORTED_SIZE);
         return nullptr;
     }
+    // FP64: a Bluestein line of M = 8192 double2 points (two buffers) does not fit one CTA
+    if (dtype == FFT3D_F64)
+        for (int L : {n0, n1, row_len})
+            if (!smooth2357(L) && L > kMaxAxis / 2) {
+                fail(FFT3D_ERR_UNSUPPORTED_SIZE);
+                return nullptr;
+            }
     if (dtype != FFT3D_F32 && (flags & (FFT3D_FLAG_EXPLICIT_TRANSPOSE | FFT3D_FLAG_GENERIC | FFT3D_FLAG_FUSED_PLANE |
                                         FFT3D_FLAG_CLUSTER_PLANE))) {
         fail(FFT3D_ERR_INVALID_ARG);  // the tensor-core forms use the plain transpose-free pass sequence
@@ -658,11 +748,13 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
     for (int i = 0; i < 3; ++i) {
         Axis& a = *axes[i];
         a.L = lens[i];
-        a.spec = (i == 2 && (n2 & 1)) ? nullptr : find_len(a.L);  // odd rows: the runtime-length kernel
-        a.tc = (dtype != FFT3D_F32 && i < 2) ? find_tc(a.L) : nullptr;
+        // odd rows and the FP64 path: the runtime-length kernels
+        a.spec = ((i == 2 && (n2 & 1)) || dtype == FFT3D_F64) ? nullptr : find_len(a.L);
+        a.tc = (is_tc_dtype(dtype) && i < 2) ? find_tc(a.L) : nullptr;
         a.gen = generic_radices(a.L);
         if (upload(forward_table(a.L, a.L), &a.d_tw) != cudaSuccess ||
-            (!smooth2357(a.L) && setup_bluestein(a) != cudaSuccess)) {
+            (!smooth2357(a.L) && setup_bluestein(a) != cudaSuccess) ||
+            (dtype == FFT3D_F64 && setup_axis64(a) != cudaSuccess)) {
             free_plan(p);
             fail(FFT3D_ERR_ALLOC);
             return nullptr;
@@ -674,7 +766,7 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
     // and wherever its column tiles are wider than the TMA kernel's
     if (p->ax0.spec && p->ax0.spec->tma_W && (p->ax0.spec->col_W > p->ax0.spec->tma_W || p->ax0.L >= 1024))
         p->choice_tma = 0;
-    if (dtype != FFT3D_F32) {
+    if (is_tc_dtype(dtype)) {
         if (!p->ax0.tc && !p->ax1.tc) {  // no axis with a tensor-core kernel: the form does not exist here
             free_plan(p);
             fail(FFT3D_ERR_UNSUPPORTED_SIZE);
@@ -689,6 +781,7 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
         }
     }
     if (upload(forward_table(n2, n2 / 2 + 1), &p->d_twpack) != cudaSuccess ||
+        (dtype == FFT3D_F64 && upload64(forward_table64(n2, n2 / 2 + 1), &p->d_twpack64) != cudaSuccess) ||
         cudaMalloc((void**)&p->d_status, sizeof(int)) != cudaSuccess ||
         cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) {
         free_plan(p);
@@ -801,7 +894,7 @@ int fft3d_query_device_status(fft3d_handle p, void* stream)
 
 int fft3d_r2c(fft3d_handle p, const float* in, void* out, void* stream)
 {
-    if (!p || !in || !out) return fail(FFT3D_ERR_INVALID_ARG);
+    if (!p || !in || !out || p->dtype == FFT3D_F64) return fail(FFT3D_ERR_INVALID_ARG);
     if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return fail(FFT3D_ERR_MISALIGNED);
     const size_t in_bytes = real_bytes(p);
     const size_t out_bytes = (size_t)p->batch * p->M * sizeof(float2);
@@ -849,7 +942,7 @@ int fft3d_r2c(fft3d_handle p, const float* in, void* out, void* stream)
 
 int fft3d_c2r(fft3d_handle p, void* in, float* out, void* stream)
 {
-    if (!p || !in || !out) return fail(FFT3D_ERR_INVALID_ARG);
+    if (!p || !in || !out || p->dtype == FFT3D_F64) return fail(FFT3D_ERR_INVALID_ARG);
     if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return fail(FFT3D_ERR_MISALIGNED);
     const size_t in_bytes = (size_t)p->batch * p->M * sizeof(float2);
     const size_t out_bytes = real_bytes(p);
@@ -916,9 +1009,63 @@ int fft3d_c2r(fft3d_handle p, void* in, float* out, void* stream)
     return FFT3D_OK;
 }
 
+// FFT3D_F64 plans: the transpose-free pass sequence of fft3d_r2c / fft3d_c2r
+// (rows, n1 columns at stride H, n0 columns at stride n1 H; the inverse in
+// reverse order), every pass on the FP64 runtime-length kernels.
+int fft3d_r2c_f64(fft3d_handle p, const double* in, void* out, void* stream)
+{
+    if (!p || !in || !out || p->dtype != FFT3D_F64) return fail(FFT3D_ERR_INVALID_ARG);
+    if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return fail(FFT3D_ERR_MISALIGNED);
+    const size_t in_bytes = (size_t)p->batch * p->n0 * p->n1 * p->n2 * sizeof(double);
+    const size_t out_bytes = (size_t)p->batch * p->M * sizeof(double2);
+    if (overlaps(in, in_bytes, out, out_bytes)) return fail(FFT3D_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long H = p->H, n0 = p->n0, n1 = p->n1, B = p->batch;
+    double2* o = (double2*)out;
+    const bool odd = p->n2 & 1;
+    RowArgs64 ra{in, out, B * n0 * n1, p->ax2.d_tw64, p->d_twpack64, odd ? (long long)p->n2 : (long long)p->n2 / 2};
+    if ((odd ? generic_row_odd64(ra, p->ax2.gen64, -1, s) : generic_row64(ra, p->ax2.gen64, -1, s)) != cudaSuccess)
+        return fail(FFT3D_ERR_CUDA);
+    if (n1 > 1) {
+        ColArgs64 ca{o, H, H, B * n0, n1 * H, p->ax1.d_tw64, nullptr};
+        if (generic_col64(ca, p->ax1.gen64, -1, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+    }
+    if (n0 > 1) {
+        ColArgs64 ca{o, p->P, p->P, B, p->M, p->ax0.d_tw64, nullptr};
+        if (generic_col64(ca, p->ax0.gen64, -1, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+    }
+    return FFT3D_OK;
+}
+
+int fft3d_c2r_f64(fft3d_handle p, void* in, double* out, void* stream)
+{
+    if (!p || !in || !out || p->dtype != FFT3D_F64) return fail(FFT3D_ERR_INVALID_ARG);
+    if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return fail(FFT3D_ERR_MISALIGNED);
+    const size_t in_bytes = (size_t)p->batch * p->M * sizeof(double2);
+    const size_t out_bytes = (size_t)p->batch * p->n0 * p->n1 * p->n2 * sizeof(double);
+    if (overlaps(in, in_bytes, out, out_bytes)) return fail(FFT3D_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long H = p->H, n0 = p->n0, n1 = p->n1, B = p->batch;
+    double2* x = (double2*)in;
+    if (n0 > 1) {
+        ColArgs64 ca{x, p->P, p->P, B, p->M, p->ax0.d_tw64, nullptr};
+        if (generic_col64(ca, p->ax0.gen64, +1, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+    }
+    if (n1 > 1) {
+        ColArgs64 ca{x, H, H, B * n0, n1 * H, p->ax1.d_tw64, nullptr};
+        if (generic_col64(ca, p->ax1.gen64, +1, s) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+    }
+    const bool odd = p->n2 & 1;
+    RowArgs64 ra{in, out, B * n0 * n1, p->ax2.d_tw64, p->d_twpack64, odd ? (long long)p->n2 : (long long)p->n2 / 2};
+    if ((odd ? generic_row_odd64(ra, p->ax2.gen64, +1, s) : generic_row64(ra, p->ax2.gen64, +1, s)) != cudaSuccess)
+        return fail(FFT3D_ERR_CUDA);
+    return FFT3D_OK;
+}
+
 int fft3d_energy(fft3d_handle p, const void* spec, double* total, double* shells, int nbins, void* stream)
 {
-    if (!p || !spec || nbins < 1 || nbins > 8192 || (!total && !shells)) return fail(FFT3D_ERR_INVALID_ARG);
+    if (!p || !spec || nbins < 1 || nbins > 8192 || (!total && !shells) || p->dtype == FFT3D_F64)
+        return fail(FFT3D_ERR_INVALID_ARG);
     if (((uintptr_t)spec & 15) || ((uintptr_t)total & 7) || ((uintptr_t)shells & 7)) return fail(FFT3D_ERR_MISALIGNED);
     const size_t need = energy_scratch_doubles(p->batch, (long long)p->n0 * p->n1, nbins);
     if (need > p->energy_doubles) {
@@ -1270,7 +1417,7 @@ int fft3d_set_plane_choice(fft3d_handle p, int cluster)
 
 int fft3d_autotune(fft3d_handle p, float* real, void* cplx, int reps, void* stream)
 {
-    if (!p || !real || !cplx) return fail(FFT3D_ERR_INVALID_ARG);
+    if (!p || !real || !cplx || p->dtype == FFT3D_F64) return fail(FFT3D_ERR_INVALID_ARG);
     if (((uintptr_t)real & 15) || ((uintptr_t)cplx & 15)) return fail(FFT3D_ERR_MISALIGNED);
     if (p->flags & (FFT3D_FLAG_GENERIC | FFT3D_FLAG_EXPLICIT_TRANSPOSE)) return FFT3D_OK;  // nothing to choose
     if (reps < 1) reps = 5;
@@ -1439,7 +1586,7 @@ int group_exec(fft3d_group_s* g, int dir, const void* const* in, void* const* ou
 
 fft3d_group_handle fft3d_plan_group(const int* dims, const int* counts, int ngroups, int dtype)
 {
-    if (!dims || !counts || ngroups < 1 || ngroups > 64) {
+    if (!dims || !counts || ngroups < 1 || ngroups > 64 || dtype == FFT3D_F64) {
         fail(FFT3D_ERR_INVALID_ARG);
         return nullptr;
     }

@@ -44,30 +44,55 @@ struct RowArgs {
                            // rows of 2H floats); in floats for odd n2 (n2 dense, 2H = n2 + 1 padded)
 };
 
-// Runtime plan for the generic (any length) kernels.  A length whose prime
-// factors are 2, 3, 5 and 7 runs its Stockham stages directly (radix list).
-// Any other length runs Bluestein's chirp-z form (M > 0): with
-// c[n] = exp(-i pi n^2 / L), the DFT is X[k] = c[k] sum_n (x[n] c[n]) conj(c[k - n]),
-// a cyclic convolution of length M (a power of two >= 2L - 1) done by two
-// length-M transforms and a pointwise product with the transformed chirp.
-struct GenPlan {
+// Runtime plan for the generic (any length) kernels, over the complex type T
+// (float2, or double2 for the FP64 path).  A length whose prime factors are
+// 2, 3, 5 and 7 runs its Stockham stages directly (radix list).  Any other
+// length runs Bluestein's chirp-z form (M > 0): with c[n] = exp(-i pi n^2 / L),
+// the DFT is X[k] = c[k] sum_n (x[n] c[n]) conj(c[k - n]), a cyclic
+// convolution of length M (a power of two >= 2L - 1) done by two length-M
+// transforms and a pointwise product with the transformed chirp.
+template <typename T>
+struct GenPlanT {
     int L;
     int nst;
     int radix[24];
-    int M;                // 0: direct stages; else the convolution length
-    int mst;              // stages of the length-M transforms
+    int M;           // 0: direct stages; else the convolution length
+    int mst;         // stages of the length-M transforms
     int mradix[24];
-    const float2* chirp;  // c[n], n < L (device)
-    const float2* bhat;   // (1/M) FFT_M of b, b[m] = b[M - m] = conj(c[m]) for m < L, else 0 (device)
-    const float2* twm;    // W_M^x = exp(-2 pi i x / M), x < M (device)
+    const T* chirp;  // c[n], n < L (device)
+    const T* bhat;   // (1/M) FFT_M of b, b[m] = b[M - m] = conj(c[m]) for m < L, else 0 (device)
+    const T* twm;    // W_M^x = exp(-2 pi i x / M), x < M (device)
 };
+using GenPlan = GenPlanT<float2>;
+using GenPlan64 = GenPlanT<double2>;
 
 // Slots per line of a generic kernel's shared buffers: the L + 1 bins of an
 // unpacked row, or the M points of a Bluestein convolution.
-__host__ __device__ inline int gen_line_slots(const GenPlan& g)
+template <typename T>
+__host__ __device__ inline int gen_line_slots(const GenPlanT<T>& g)
 {
     return g.M > g.L + 1 ? g.M : g.L + 1;
 }
+
+// Arguments of the FP64 passes (runtime-length kernels only): as ColArgs and
+// RowArgs, in double precision, without scaling, masking or status word.
+struct ColArgs64 {
+    double2* data;       // in place
+    long long S;         // axis stride (complex elements)
+    long long C;         // contiguous columns per batch entry
+    long long nb;        // batch entries
+    long long Bs;        // batch stride (complex elements)
+    const double2* tw;   // W_L^m, m in [0, L)
+    double2* dst;        // nullptr: in place
+};
+struct RowArgs64 {
+    const void* in;
+    void* out;
+    long long rows;
+    const double2* tw;      // W_L^m, m in [0, L), L = n2/2 (even n2) or n2 (odd n2)
+    const double2* twpack;  // exp(-2 pi i k / n2), k in [0, L] (even n2)
+    long long rs;           // real-side row stride: in double pairs for even n2, in doubles for odd n2
+};
 
 // Launchers take a runtime shape choice: w = columns per CTA (0 or > compiled
 // maximum: the compiled value), rows = rows per CTA (same rule).
@@ -126,5 +151,8 @@ const TcEntry* tc_entries(int* n);
 cudaError_t generic_col(const ColArgs& a, const GenPlan& g, int dir, cudaStream_t s);
 cudaError_t generic_row(const RowArgs& a, const GenPlan& g, int dir, cudaStream_t s);
 cudaError_t generic_row_odd(const RowArgs& a, const GenPlan& g, int dir, cudaStream_t s);
+cudaError_t generic_col64(const ColArgs64& a, const GenPlan64& g, int dir, cudaStream_t s);
+cudaError_t generic_row64(const RowArgs64& a, const GenPlan64& g, int dir, cudaStream_t s);
+cudaError_t generic_row_odd64(const RowArgs64& a, const GenPlan64& g, int dir, cudaStream_t s);
 
 }  // namespace fft3d

@@ -41,8 +41,13 @@ def test_plan_rejects_bad_sizes_before_touching_the_device(lib, dims, status):
 
 
 def test_plan_rejects_bad_dtype_batch_flags(lib):
-    assert not fft3d.fft3d_plan(8, 8, 8, 3, 1)
+    assert not fft3d.fft3d_plan(8, 8, 8, 4, 1)
     assert fft3d.fft3d_last_error() == fft3d.FFT3D_ERR_INVALID_ARG
+    # FP64 plans take no flags, and no Bluestein length above 2048
+    assert not fft3d.fft3d_plan_variant(8, 8, 8, fft3d.FFT3D_F64, 1, fft3d.FFT3D_FLAG_PADDED_REAL)
+    assert fft3d.fft3d_last_error() == fft3d.FFT3D_ERR_INVALID_ARG
+    assert not fft3d.fft3d_plan(2053, 8, 8, fft3d.FFT3D_F64, 1)
+    assert fft3d.fft3d_last_error() == fft3d.FFT3D_ERR_UNSUPPORTED_SIZE
     assert not fft3d.fft3d_plan(8, 8, 8, 7, 1)
     assert fft3d.fft3d_last_error() == fft3d.FFT3D_ERR_INVALID_ARG
     assert not fft3d.fft3d_plan(8, 8, 8, 0, 0)
@@ -63,6 +68,8 @@ def test_nonlinear_plan_rejects_bad_sizes(lib):
 def test_null_handles(lib):
     assert fft3d.fft3d_r2c(None, 16, 32) == fft3d.FFT3D_ERR_INVALID_ARG
     assert fft3d.fft3d_c2r(None, 16, 32) == fft3d.FFT3D_ERR_INVALID_ARG
+    assert fft3d.fft3d_r2c_f64(None, 16, 32) == fft3d.FFT3D_ERR_INVALID_ARG
+    assert fft3d.fft3d_c2r_f64(None, 16, 32) == fft3d.FFT3D_ERR_INVALID_ARG
     assert fft3d.fft3d_workspace_bytes(None) == 0
     assert fft3d.fft3d_set_workspace(None, 0) == fft3d.FFT3D_ERR_INVALID_ARG
     assert fft3d.fft3d_launches_per_call(None) == fft3d.FFT3D_ERR_INVALID_ARG

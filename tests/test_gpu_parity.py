@@ -738,6 +738,73 @@ def test_long_axis_column_forms_match_oracle(cuda_lib, shape):
     plan.close()
 
 
+# ---------------------------------------------------------------------------
+# FP64 path (FFT3D_F64): every pass on the FP64 runtime-length kernels.
+# ---------------------------------------------------------------------------
+TOL_F64 = 1e-12
+
+F64_SHAPES = [((32, 32, 32), 1), ((48, 80, 96), 1), ((6, 10, 15), 1), ((11, 13, 22), 1), ((3, 97, 8), 1),
+              ((14, 7, 9), 2), ((64, 64, 64), 2), ((2, 2, 4094), 1), ((4096, 2, 2), 1), ((2, 2, 8192), 1)]
+
+
+@pytest.mark.parametrize("shape,batch", F64_SHAPES, ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else f"b{v}")
+def test_fp64_path_matches_oracle(cuda_lib, shape, batch):
+    """FFT3D_F64: r2c against the FP64 oracle, c2r of an arbitrary half
+    spectrum against the oracle's c2r, and the round trip, at 1e-12 (the FP32
+    path stays near 1e-7): direct and Bluestein lengths (11, 13, 97, 2047 =
+    23 x 89), odd n2, batch, the longest lines (4096 points; a Bluestein line
+    of 4096)."""
+    lib = cuda_lib
+    n0, n1, n2 = shape
+    H = n2 // 2 + 1
+    plan = lib.Plan(n0, n1, n2, dtype=lib.FFT3D_F64, batch=batch)
+    assert plan.describe().split()[2] == "fp64"
+    x = synth.uniform_field((batch, n0, n1, n2), seed=83)
+    xd = torch.from_numpy(x).cuda()
+    X = torch.empty((batch, n0, n1, H), dtype=torch.complex128, device="cuda")
+    plan.r2c(xd.data_ptr(), X.data_ptr())
+    torch.cuda.synchronize()
+    assert rel_l2(X.cpu().numpy(), oracle.r2c3d(x)) <= TOL_F64
+    y = torch.empty_like(xd)
+    plan.c2r(X.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    assert rel_l2(y.cpu().numpy() / (n0 * n1 * n2), x) <= TOL_F64
+    Y = random_half_spectrum((batch * n0, n1, H), seed=84).astype(np.complex128).reshape(batch, n0, n1, H)
+    Yd = torch.from_numpy(Y).cuda()
+    plan.c2r(Yd.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    assert rel_l2(y.cpu().numpy(), oracle.c2r3d(Y, n2)) <= TOL_F64
+    plan.close()
+
+
+def test_fp64_entry_points_and_helpers(cuda_lib):
+    """FP64 plans go through fft3d_r2c_f64 / fft3d_c2r_f64 only (and FP32
+    plans never do); the forms built on FP32 spectra reject FP64 plans; rfft3
+    / irfft3 pick the FP64 path for float64 / complex128 tensors."""
+    lib = cuda_lib
+    p64 = lib.Plan(8, 8, 8, dtype=lib.FFT3D_F64)
+    p32 = lib.Plan(8, 8, 8)
+    a = torch.zeros(8 * 8 * 8 * 2, dtype=torch.float64, device="cuda")
+    b = torch.zeros(8 * 8 * 5 * 2, dtype=torch.float64, device="cuda")
+    assert lib.fft3d_r2c(p64.handle, a.data_ptr(), b.data_ptr(), 0) == lib.FFT3D_ERR_INVALID_ARG
+    assert lib.fft3d_c2r(p64.handle, b.data_ptr(), a.data_ptr(), 0) == lib.FFT3D_ERR_INVALID_ARG
+    assert lib.fft3d_r2c_f64(p32.handle, a.data_ptr(), b.data_ptr(), 0) == lib.FFT3D_ERR_INVALID_ARG
+    assert lib.fft3d_c2r_f64(p32.handle, b.data_ptr(), a.data_ptr(), 0) == lib.FFT3D_ERR_INVALID_ARG
+    assert lib.fft3d_r2c_f64(p64.handle, a.data_ptr(), a.data_ptr() + 64, 0) == lib.FFT3D_ERR_INVALID_ARG
+    with pytest.raises(lib.Fft3dError):
+        p64.energy(torch.zeros((8, 8, 5), dtype=torch.complex64, device="cuda"), 4)
+    assert lib.fft3d_autotune(p64.handle, a.data_ptr(), b.data_ptr(), 1) == lib.FFT3D_ERR_INVALID_ARG
+    p64.close()
+    p32.close()
+    x = torch.from_numpy(synth.uniform_field((2, 12, 10, 14), seed=85)).cuda()
+    X = lib.rfft3(x)
+    assert X.dtype == torch.complex128
+    assert rel_l2(X.cpu().numpy(), oracle.r2c3d(x.cpu().numpy())) <= TOL_F64
+    y = lib.irfft3(X, 14)
+    assert y.dtype == torch.float64
+    assert rel_l2(y.cpu().numpy() / (12 * 10 * 14), x.cpu().numpy()) <= TOL_F64
+
+
 def test_tuned_plan_uses_the_cache(cuda_lib, tmp_path):
     from paper_1406_5597_gb300 import tune
     path = str(tmp_path / "wisdom.json")
