@@ -38,6 +38,14 @@
  * Errors: functions returning int return an fft3d_status.  Argument errors
  * are found before any launch and leave the output untouched.  The status of
  * the last failing call on the calling thread is kept for fft3d_last_error.
+ *
+ * Tracing and environment: every pass is enclosed in an NVTX range named for
+ * the pass ("row_r2c", "col_n1_fwd", "col_n0_fwd", ...; see fft3d_pass_name)
+ * around its launch.  FFT3D_LOG=1 prints each plan's kernel choices and each
+ * autotune result on stderr.  FFT3D_FORCE_PASSES (a test and benchmark
+ * override, read at every plan creation) ORs forms into the flags of every
+ * FP32 plan: a comma-separated list of "three", "generic", "fused", "cluster",
+ * "transpose", "transpose_back" (the FFT3D_FLAG_* forms of the same names).
  */
 #ifndef FFT3D_H
 #define FFT3D_H

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include <cuda_bf16.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_fp16.h>
 
 #include "args.h"
@@ -63,6 +64,47 @@ int fail(int status)
 {
     g_last_error = status;
     return status;
+}
+
+// FFT3D_LOG=1: planner and autotuner decisions on stderr.
+bool log_enabled()
+{
+    static const bool on = [] {
+        const char* v = std::getenv("FFT3D_LOG");
+        return v && *v && std::strcmp(v, "0") != 0;
+    }();
+    return on;
+}
+
+// FFT3D_FORCE_PASSES: a test / benchmark override of the planner, read at every
+// plan creation: comma-separated forms OR-ed into the flags of every FP32 plan
+// ("three", "generic", "fused", "cluster", "transpose", "transpose_back";
+// unknown names are ignored).  Combinations that are invalid for a plan fail
+// as if passed as flags.
+int forced_flags()
+{
+    const char* v = std::getenv("FFT3D_FORCE_PASSES");
+    if (!v) return 0;
+    static const struct {
+        const char* name;
+        int flags;
+    } forms[] = {{"three", FFT3D_FLAG_THREE_PASS},
+                 {"generic", FFT3D_FLAG_GENERIC},
+                 {"fused", FFT3D_FLAG_FUSED_PLANE},
+                 {"cluster", FFT3D_FLAG_CLUSTER_PLANE},
+                 {"transpose", FFT3D_FLAG_EXPLICIT_TRANSPOSE},
+                 {"transpose_back", FFT3D_FLAG_EXPLICIT_TRANSPOSE | FFT3D_FLAG_TRANSPOSE_BACK}};
+    int f = 0;
+    std::string s(v);
+    size_t pos = 0;
+    while (pos <= s.size()) {
+        const size_t end = s.find(',', pos) == std::string::npos ? s.size() : s.find(',', pos);
+        const std::string tok = s.substr(pos, end - pos);
+        for (const auto& m : forms)
+            if (tok == m.name) f |= m.flags;
+        pos = end + 1;
+    }
+    return f;
 }
 
 bool smooth2357(long long n)
@@ -419,12 +461,15 @@ void free_plan(fft3d_plan_s* p)
 }
 
 // Brackets one launch with events when the plan is profiling.
+// One pass: an NVTX range named for the pass around its launch (host side,
+// seen by a tracing tool), and CUDA events around it while profiling is on.
 struct ProfScope {
     fft3d_plan_s* p;
     ProfRecord* r = nullptr;
     cudaStream_t s;
     ProfScope(fft3d_plan_s* plan, int pass, cudaStream_t stream) : p(plan), s(stream)
     {
+        nvtxRangePushA(kPassNames[pass]);
         if (!p->profiling) return;
         if (p->prof_used == p->prof.size()) {
             ProfRecord nr{pass, nullptr, nullptr};
@@ -438,6 +483,7 @@ struct ProfScope {
     ~ProfScope()
     {
         if (r) cudaEventRecord(r->b, s);
+        nvtxRangePop();
     }
 };
 
@@ -693,6 +739,7 @@ int fft3d_last_error(void) { return g_last_error; }
 
 fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, int flags)
 {
+    if (dtype != FFT3D_F64) flags |= forced_flags();
     if (n0 < 1 || n1 < 1 || n2 < 2 || batch < 1 || dtype < 0 || dtype > FFT3D_F64 ||
         (dtype == FFT3D_F64 && flags != 0) ||
         (flags & ~(FFT3D_FLAG_EXPLICIT_TRANSPOSE | FFT3D_FLAG_TRANSPOSE_BACK | FFT3D_FLAG_THREE_PASS |
@@ -832,6 +879,9 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
         }
     }
     p->desc = describe_plan(p);
+    if (log_enabled())
+        std::fprintf(stderr, "fft3d: plan %dx%dx%d batch=%d dtype=%d flags=0x%x: %s\n", n0, n1, n2, batch, dtype, flags,
+                     p->desc.c_str());
     return p;
 }
 
@@ -1492,6 +1542,11 @@ int fft3d_autotune(fft3d_handle p, float* real, void* cplx, int reps, void* stre
         p->cplane = best_e;
     }
     p->profiling = prof;
+    p->desc = describe_plan(p);
+    if (log_enabled())
+        std::fprintf(stderr, "fft3d: autotune %dx%dx%d: choices {%d, %d, %d, %d, %d} plane C=%d: %s\n", p->n0, p->n1,
+                     p->n2, p->choice_w0, p->choice_w1, p->choice_rows, p->choice_tma, p->choice_tma1,
+                     p->cplane ? p->cplane->C : 0, p->desc.c_str());
     return cudaGetLastError() == cudaSuccess ? FFT3D_OK : fail(FFT3D_ERR_CUDA);
 }
 

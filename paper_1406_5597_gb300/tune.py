@@ -3,7 +3,7 @@
 fft3d_autotune (C) times the candidate shapes of every pass on the caller's
 buffers and keeps the fastest; this module stores the chosen six integers
 {w0, w1, rows, tma0, tma1, plane cluster size} in a JSON file so later plans of
-the same GPU model and shape reuse them without tuning.  File: $FFT3D_TUNE_CACHE, else
+the same GPU model, driver and shape reuse them without tuning.  File: $FFT3D_TUNE_CACHE, else
 ~/.cache/fft3d_wisdom.json.
 """
 from __future__ import annotations
@@ -21,9 +21,24 @@ def cache_path() -> str:
                                                                "fft3d_wisdom.json")
 
 
-def cache_key(gpu: str, shape, batch: int, dtype: int, flags: int) -> str:
+def driver_version() -> int:
+    """The CUDA driver's version number (cuDriverGetVersion), 0 if unknown."""
+    import ctypes
+    try:
+        v = ctypes.c_int(0)
+        if ctypes.CDLL("libcuda.so.1").cuDriverGetVersion(ctypes.byref(v)) != 0:
+            return 0
+        return v.value
+    except OSError:
+        return 0
+
+
+def cache_key(gpu: str, shape, batch: int, dtype: int, flags: int, driver: int | None = None) -> str:
+    """Entries are per GPU model and driver (a new driver may change which
+    kernel shape is fastest), shape, batch, dtype and flags."""
     n0, n1, n2 = shape
-    return f"{gpu}|{n0}x{n1}x{n2}|b{batch}|d{dtype}|f{flags}"
+    drv = driver_version() if driver is None else driver
+    return f"{gpu}|drv{drv}|{n0}x{n1}x{n2}|b{batch}|d{dtype}|f{flags}"
 
 
 def load_cache(path: str | None = None) -> dict:

@@ -21,3 +21,11 @@ def test_corrupt_cache_reads_empty(tmp_path):
     p = tmp_path / "w.json"
     p.write_text("{not json")
     assert tune.load_cache(str(p)) == {}
+
+
+def test_cache_key_separates_drivers():
+    """A new driver may change the fastest kernel shape: keys differ by driver."""
+    a = tune.cache_key("NVIDIA GB300", (512, 512, 512), 1, 0, 0, driver=13000)
+    b = tune.cache_key("NVIDIA GB300", (512, 512, 512), 1, 0, 0, driver=13010)
+    assert a != b and "drv13000" in a
+    assert isinstance(tune.driver_version(), int)  # 0 where no driver is installed
