@@ -1,7 +1,7 @@
 """One-shot driver: a plan, one forward r2c and one inverse c2r on seeded
 random data on the current CUDA device, through the C ABI.
 
-    python -m paper_1406_5597_gb300 --shape 512,512,512 [--flags 0x40] [--dtype f32|bf16x3|f16]
+    python -m paper_1406_5597_gb300 --shape 512,512,512 [--flags 0x40] [--dtype f32|bf16x3|f16|f64]
     python -m paper_1406_5597_gb300 --shape 256,256,256 --ns
 
 Prints the plan description and the round-trip relative L2 error
@@ -14,7 +14,7 @@ import argparse
 
 import torch
 
-from . import FFT3D_F32, FFT3D_F32_TC_BF16X3, FFT3D_F32_TC_F16, NavierStokes, Plan, load
+from . import FFT3D_F32, FFT3D_F32_TC_BF16X3, FFT3D_F32_TC_F16, FFT3D_F64, NavierStokes, Plan, load
 
 
 def main() -> None:
@@ -22,12 +22,13 @@ def main() -> None:
     ap.add_argument("--shape", default="512,512,512", help="n0,n1,n2")
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--flags", type=lambda v: int(v, 0), default=0, help="FFT3D_FLAG_* bits")
-    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16x3", "f16"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16x3", "f16", "f64"])
     ap.add_argument("--seed", type=int, default=1408)
     ap.add_argument("--ns", action="store_true", help="one Navier-Stokes step instead of r2c + c2r")
     args = ap.parse_args()
     n0, n1, n2 = (int(v) for v in args.shape.split(","))
-    dtype = {"f32": FFT3D_F32, "bf16x3": FFT3D_F32_TC_BF16X3, "f16": FFT3D_F32_TC_F16}[args.dtype]
+    dtype = {"f32": FFT3D_F32, "bf16x3": FFT3D_F32_TC_BF16X3, "f16": FFT3D_F32_TC_F16, "f64": FFT3D_F64}[args.dtype]
+    rt, ct = (torch.float64, torch.complex128) if dtype == FFT3D_F64 else (torch.float32, torch.complex64)
     load()
     dev = torch.device("cuda", torch.cuda.current_device())
     gen = torch.Generator(device=dev)
@@ -41,8 +42,8 @@ def main() -> None:
         ns.close()
         return
     lead = (args.batch,) if args.batch > 1 else ()
-    x = torch.randn(lead + (n0, n1, n2), device=dev, generator=gen)
-    X = torch.empty(lead + (n0, n1, n2 // 2 + 1), dtype=torch.complex64, device=dev)
+    x = torch.randn(lead + (n0, n1, n2), device=dev, generator=gen, dtype=rt)
+    X = torch.empty(lead + (n0, n1, n2 // 2 + 1), dtype=ct, device=dev)
     y = torch.empty_like(x)
     plan = Plan(n0, n1, n2, dtype, args.batch, args.flags)
     s = torch.cuda.current_stream(dev).cuda_stream
