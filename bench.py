@@ -152,6 +152,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+SLOWDOWN_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def clocks_rejected(clocks, world=1):
+    """A timed region whose clock record shows a hardware or thermal slowdown,
+    or SM clocks well below their maximum with no reason given (a clock lock
+    left by someone else), is not a valid measurement.  Under torchrun every
+    rank must take the same decision, so the verdict is max-reduced."""
+    bad = bool(clocks) and (any(r in clocks["reasons"] for r in SLOWDOWN_REASONS)
+                            or (not clocks["reasons"] and clocks["sm_mhz"] < 0.9 * clocks["sm_max_mhz"]))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([1 if bad else 0], device=torch.device("cuda", torch.cuda.current_device()))
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        bad = bool(t.item())
+    return bad
+
+
 def make_field(n):
     """Spectrum-shaped half spectrum S (complex64 numpy) of velocity component 0."""
     return make_field_shape(n, n, n)
@@ -287,20 +306,28 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler = ClockSampler(local_rank)
-    sampler.start()
-    time.sleep(1.0)
-    fft3d.fft3d_set_profiling(plan.handle, True)
-    ms_total = time_steps(step, stream, args.steps)
-    fft3d.fft3d_set_profiling(plan.handle, False)
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    prof = fft3d.fft3d_profile_read(plan.handle)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-        dist.barrier()
+    def timed_region():
+        sampler = ClockSampler(local_rank)
+        sampler.start()
+        time.sleep(1.0)
+        fft3d.fft3d_set_profiling(plan.handle, True)
+        ms_total = time_steps(step, stream, args.steps)
+        fft3d.fft3d_set_profiling(plan.handle, False)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        prof = fft3d.fft3d_profile_read(plan.handle)
+        if world > 1:
+            t = torch.tensor([ms_total], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_total = float(t.item())
+            dist.barrier()
+        return ms_total, clocks, prof
+
+    ms_total, clocks, prof = timed_region()
+    first = None
+    if clocks_rejected(clocks, world):  # a slowed-down or clock-locked GPU: measure once more
+        first = {"ms_per_step": ms_total / args.steps, "clocks": clocks}
+        ms_total, clocks, prof = timed_region()
     ms = ms_total / args.steps
     value = world * nbytes / (ms * 1e-3) / 1e9
     launches = args.steps * (fft3d.fft3d_launches_per_call(plan.handle, -1) + fft3d.fft3d_launches_per_call(plan.handle, 1))
@@ -328,6 +355,8 @@ def main():
         "plan": plan.describe(), "choices": fft3d.fft3d_get_choices(plan.handle),
         "autotuned": not args.no_autotune,
     }
+    if first is not None:
+        line["remeasured"] = {"reason": "clock record of the first timed region rejected", "first": first}
 
     # comparator: the explicit-transpose variant (+1 pass), and with transpose-back (+2)
     if not args.no_variants:

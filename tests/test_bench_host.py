@@ -53,3 +53,16 @@ def test_reference_arm_other_ranks_do_no_work():
     r = _run(["--impl", "reference", "--n", "16", "--steps", "1"], env={"RANK": "1", "WORLD_SIZE": "2",
                                                                           "LOCAL_RANK": "1"})
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_clock_records_that_void_a_measurement():
+    """Slowdown reasons, or clocks far below max with no reason (a leftover
+    lock), reject the timed region; the power cap alone does not."""
+    import bench
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 10}
+    assert not bench.clocks_rejected(ok)
+    assert not bench.clocks_rejected(None)
+    assert not bench.clocks_rejected(dict(ok, sm_mhz=1800.0, reasons=["sw_power_cap"]))
+    assert bench.clocks_rejected(dict(ok, reasons=["hw_slowdown"]))
+    assert bench.clocks_rejected(dict(ok, reasons=["sw_thermal_slowdown", "sw_power_cap"]))
+    assert bench.clocks_rejected(dict(ok, sm_mhz=1200.0))
