@@ -323,7 +323,7 @@ def test_padded_real_layout_in_and_out_of_place(cuda_lib, shape, extra):
 
 
 @pytest.mark.parametrize("shape,plane", [((32, 32, 32), 0), ((5, 128, 128), 2), ((1, 8, 16), 0), ((4, 1, 8), 0),
-                                         ((6, 512, 60), 0), ((64, 64, 64), 1)],
+                                         ((6, 512, 60), 0), ((64, 64, 64), 1), ((11, 13, 22), 0), ((7, 5, 9), 0)],
                          ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else f"plane{v}")
 def test_preserve_input_c2r(cuda_lib, shape, plane):
     """FFT3D_FLAG_PRESERVE_INPUT: c2r leaves its input bit for bit unchanged
@@ -470,23 +470,29 @@ def test_batched_tma_column_pass(cuda_lib):
         assert rel_l2(y[b], oracle.c2r3d(Y[b].astype(np.complex128), 12)) <= TOL
 
 
-def test_batch_entries_do_not_bleed(cuda_lib):
-    shape = (3, 16, 24, 20)
+@pytest.mark.parametrize("shape", [(3, 16, 24, 20), (3, 11, 13, 22), (2, 6, 10, 15), (2, 5, 17, 9)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_batch_entries_do_not_bleed(cuda_lib, shape):
+    """Batch offsets on specialised, Bluestein (11, 13, 17) and odd-n2 paths."""
+    B, n0, n1, n2 = shape
+    H = n2 // 2 + 1
     x32 = synth.uniform_field(shape, seed=37).astype(np.float32)
     X = gpu_r2c(cuda_lib, x32)
-    for b in range(3):
+    for b in range(B):
         assert rel_l2(X[b], oracle.r2c3d(x32[b].astype(np.float64))) <= TOL
-    Y = random_half_spectrum((3 * 16, 24, 11), seed=41).reshape(3, 16, 24, 11)
-    y = gpu_c2r(cuda_lib, Y, 20)
-    for b in range(3):
-        assert rel_l2(y[b], oracle.c2r3d(Y[b].astype(np.complex128), 20)) <= TOL
+    Y = random_half_spectrum((B * n0, n1, H), seed=41).reshape(B, n0, n1, H)
+    y = gpu_c2r(cuda_lib, Y, n2)
+    for b in range(B):
+        assert rel_l2(y[b], oracle.c2r3d(Y[b].astype(np.complex128), n2)) <= TOL
 
 
-def test_impulses_map_to_plane_waves(cuda_lib):
+@pytest.mark.parametrize("shape", [(24, 40, 36), (11, 13, 26)], ids=lambda s: "x".join(map(str, s)))
+def test_impulses_map_to_plane_waves(cuda_lib, shape):
     """A delta at (j0, j1, j2) transforms to exp(-2 pi i k.j/n): checks every
-    index placement, including the rows and columns at the tile edges."""
-    shape = (24, 40, 36)
-    for j in [(0, 0, 0), (23, 39, 35), (5, 17, 1), (12, 20, 18)]:
+    index placement, including the rows and columns at the tile edges (and,
+    at 11 x 13 x 26, the Bluestein chirp indices)."""
+    n0, n1, n2 = shape
+    for j in [(0, 0, 0), (n0 - 1, n1 - 1, n2 - 1), (5, 7, 1), (n0 // 2, n1 // 2, n2 // 2)]:
         x32 = synth.delta_field(*shape, *j).astype(np.float32)
         X = gpu_r2c(cuda_lib, x32)
         assert rel_l2(X, oracle.r2c3d(x32.astype(np.float64))) <= TOL
@@ -501,8 +507,9 @@ def test_c2r_ignores_imag_of_dc_and_nyquist_bins(cuda_lib):
 
 
 @pytest.mark.parametrize("back", [False, True])
-def test_explicit_transpose_variant(cuda_lib, back):
-    n0, n1, n2 = 32, 48, 40
+@pytest.mark.parametrize("shape", [(32, 48, 40), (11, 13, 22)], ids=lambda s: "x".join(map(str, s)))
+def test_explicit_transpose_variant(cuda_lib, back, shape):
+    n0, n1, n2 = shape
     f = cuda_lib.FFT3D_FLAG_EXPLICIT_TRANSPOSE | (cuda_lib.FFT3D_FLAG_TRANSPOSE_BACK if back else 0)
     x32 = synth.uniform_field((n0, n1, n2), seed=47).astype(np.float32)
     X = gpu_r2c(cuda_lib, x32, flags=f)
