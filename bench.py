@@ -155,7 +155,17 @@ class ClockSampler:
 SLOWDOWN_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
 
 
-def clocks_rejected(clocks, world=1):
+def max_over_ranks(values, device):
+    """Element-wise maximum of a list of numbers over all ranks of the process
+    group (the job's time is that of its slowest rank); every rank gets it."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def clocks_rejected(clocks, world=1, device=None):
     """A timed region whose clock record shows a hardware or thermal slowdown,
     or SM clocks well below their maximum with no reason given (a clock lock
     left by someone else), is not a valid measurement.  Under torchrun every
@@ -163,11 +173,7 @@ def clocks_rejected(clocks, world=1):
     bad = bool(clocks) and (any(r in clocks["reasons"] for r in SLOWDOWN_REASONS)
                             or (not clocks["reasons"] and clocks["sm_mhz"] < 0.9 * clocks["sm_max_mhz"]))
     if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([1 if bad else 0], device=torch.device("cuda", torch.cuda.current_device()))
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        bad = bool(t.item())
+        bad = max_over_ranks([1.0 if bad else 0.0], device)[0] > 0.0
     return bad
 
 
@@ -317,15 +323,13 @@ def main():
         clocks = sampler.stop()
         prof = fft3d.fft3d_profile_read(plan.handle)
         if world > 1:
-            t = torch.tensor([ms_total], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_total = float(t.item())
+            ms_total = max_over_ranks([ms_total], dev)[0]
             dist.barrier()
         return ms_total, clocks, prof
 
     ms_total, clocks, prof = timed_region()
     first = None
-    if clocks_rejected(clocks, world):  # a slowed-down or clock-locked GPU: measure once more
+    if clocks_rejected(clocks, world, dev):  # a slowed-down or clock-locked GPU: measure once more
         first = {"ms_per_step": ms_total / args.steps, "clocks": clocks}
         ms_total, clocks, prof = timed_region()
     ms = ms_total / args.steps
@@ -620,9 +624,7 @@ def main():
         torch.cuda.synchronize()
         sms_ = time_steps(estep, stream, max(5, args.steps // 4)) / max(5, args.steps // 4)
         if world > 1:
-            t = torch.tensor([ems, sms_], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems, sms_ = float(t[0].item()), float(t[1].item())
+            ems, sms_ = max_over_ranks([ems, sms_], dev)
         line["e2e"] = {"value": world * nbytes / (ems * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ems,
                        "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N,
                        "mode": "stream of steps, double-buffered: copies in / out on their own streams",

@@ -66,3 +66,38 @@ def test_clock_records_that_void_a_measurement():
     assert bench.clocks_rejected(dict(ok, reasons=["hw_slowdown"]))
     assert bench.clocks_rejected(dict(ok, reasons=["sw_thermal_slowdown", "sw_power_cap"]))
     assert bench.clocks_rejected(dict(ok, sm_mhz=1200.0))
+
+
+def _free_port():
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _reduction_worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        times = bench.max_over_ranks([1.0 + rank, 5.0 - rank], "cpu")
+        ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+        bad = bench.clocks_rejected(dict(ok, reasons=["hw_slowdown"]) if rank == 0 else ok, world, "cpu")
+        clean = bench.clocks_rejected(ok, world, "cpu")
+        with open(os.path.join(out_dir, f"rank{rank}.json"), "w") as f:
+            json.dump({"times": times, "bad": bad, "clean": clean}, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_cross_rank_reductions_on_two_gloo_ranks(tmp_path):
+    """The N > 1 bench path on CPU ranks: every rank gets the slowest rank's
+    times, and a clock record rejected on one rank makes every rank measure
+    again (the ranks never disagree on whether to re-run)."""
+    import torch
+    torch.multiprocessing.spawn(_reduction_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    for rank in range(2):
+        r = json.load(open(tmp_path / f"rank{rank}.json"))
+        assert r["times"] == [2.0, 5.0]
+        assert r["bad"] is True and r["clean"] is False
