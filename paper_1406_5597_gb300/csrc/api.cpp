@@ -36,13 +36,14 @@ const LenEntry* entries_small(int* n);
 const LenEntry* entries_mixed(int* n);
 const LenEntry* entries_256_512(int* n);
 const LenEntry* entries_1024_2048(int* n);
+const LenEntry* entries_mixed_wide(int* n);
 cudaError_t launch_swap01(const float2* in, float2* out, long long batch, long long n0, long long n1, long long H,
                           cudaStream_t s);
 
 const LenEntry* find_len(int L)
 {
     using Fn = const LenEntry* (*)(int*);
-    static const Fn groups[] = {entries_small, entries_mixed, entries_256_512, entries_1024_2048};
+    static const Fn groups[] = {entries_small, entries_mixed, entries_256_512, entries_1024_2048, entries_mixed_wide};
     for (Fn f : groups) {
         int n = 0;
         const LenEntry* e = f(&n);

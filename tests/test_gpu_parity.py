@@ -133,6 +133,10 @@ SHAPES = [
     (2, 2048, 32), (2, 2048, 30),
     # a factor 7 on every axis (runtime-radix kernels, radix-7 codelet)
     (14, 28, 56), (7, 7, 14), (49, 6, 28), (112, 3, 98), (5, 21, 70),
+    # compile-time kernels for 3 * 2^k and 5 * 2^k lengths: columns (n0 and n1,
+    # ragged tiles) and warp-resident rows (n2 / 2 = 160 .. 768)
+    (320, 4, 6), (4, 320, 10), (384, 5, 7), (3, 384, 4), (640, 2, 4), (2, 640, 6), (768, 2, 4), (2, 768, 3),
+    (1280, 2, 4), (2, 1280, 4), (2, 3, 320), (2, 3, 384), (2, 3, 640), (2, 2, 768), (2, 2, 1280), (2, 2, 1536),
     # prime factors above 7 (Bluestein form): every axis, odd and even n2, ragged
     # column tiles, and the longest prime lengths (M = 8192)
     (11, 13, 22), (17, 4, 26), (6, 97, 8), (4, 6, 13), (3, 1021, 4), (143, 3, 10), (2, 2, 8186), (4093, 2, 3),
@@ -272,7 +276,7 @@ def test_plane_form_every_cluster_size_and_autotune(cuda_lib, shape):
 
 
 PADDED_SHAPES = [(32, 32, 32), (64, 64, 64), (6, 512, 60), (8, 6, 1024), (3, 2, 2048), (2, 3, 4096), (48, 80, 96),
-                 (5, 3, 2), (1, 8, 16), (4, 6, 9), (3, 5, 15), (4, 6, 26), (3, 11, 13)]
+                 (5, 3, 2), (1, 8, 16), (4, 6, 9), (3, 5, 15), (4, 6, 26), (3, 11, 13), (4, 3, 768), (2, 5, 640)]
 
 
 @pytest.mark.parametrize("extra", ["plain", "generic", "tc"])
