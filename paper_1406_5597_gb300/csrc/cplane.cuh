@@ -107,7 +107,7 @@ struct CPlaneGeom {
     static constexpr int RC = LC / C;                      // slab rows per CTA
     static constexpr int SH = H + (24 - H % 16) % 16;      // slab row stride: 64 bytes past a 128-byte multiple
     static constexpr int TR = LR / ER;                     // threads per row transform
-    static constexpr int RPR = NT / TR;                    // rows per round (round 0 comes through the stage)
+    static constexpr int RPR = NT / TR;                    // rows per wave (wave 0 comes through the stage)
     static constexpr int ROUNDS = RC / RPR;
     static constexpr int EC = (RC <= 32 && num_stages(RC, RC) == 1) ? RC : 16;  // column transform: elements
                                                            // per thread (one thread per column when a single
@@ -130,7 +130,7 @@ struct CPlaneGeom {
     static constexpr size_t smem_inv = (size_t)SLAB * sizeof(float2);
     static_assert(LC % C == 0 && RC >= C, "n1 must split evenly over the cluster");
     static_assert(TR <= 32 && 32 % TR == 0 && NT % 32 == 0, "rows must pack into warps");
-    static_assert(RPR <= RC && RC % RPR == 0, "row rounds must tile the slab rows");
+    static_assert(RPR <= RC && RC % RPR == 0, "row waves must tile the slab rows");
     static_assert(RC % EC == 0 && TC <= 32 && 32 % TC == 0, "column transform must pack into warps");
     static_assert(num_stages(RC, EC) > 0, "RC must factor into radices dividing 16");
     static_assert((LR - 1) + (LR - 1) / 32 < SH, "row exchange must fit a slab row");
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(NT, MINB) cplane_kernel(CPlaneArgs a)
     // this CTA's k' rows in the radix-C step
     const int kbase = (int)rank * RC / C;
     const int NX = ((int)rank + 1) * RC / C * H - kbase * H;
-    // row rounds: thread (rr, tr) transforms slab row r*RPR + rr
+    // row waves: thread (rr, tr) transforms slab row r*RPR + rr
     const int rr = tid / TR, tr = tid - (tid / TR) * TR;
     // column groups: lane (cc, tc) of a warp, GC columns per group
     const int cc = lane % GC, tc = lane / GC;
@@ -186,8 +186,8 @@ __global__ void __launch_bounds__(NT, MINB) cplane_kernel(CPlaneArgs a)
     };
 
     if constexpr (DIR < 0) {
-        // Forward.  Input rows of a plane: round 0 arrives by bulk copies in
-        // the stage buffer during the previous plane; rounds 1.. arrive in
+        // Forward.  Input rows of a plane: wave 0 arrives by bulk copies in
+        // the stage buffer during the previous plane; waves 1.. arrive in
         // place, each real row in the slab row that later holds its spectrum.
         float2* stage = reinterpret_cast<float2*>(smraw + (size_t)G::SLAB * sizeof(float2));
         unsigned long long* bars = reinterpret_cast<unsigned long long*>(smraw + (size_t)G::SLAB * sizeof(float2) +
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(NT, MINB) cplane_kernel(CPlaneArgs a)
                 mbar_arrive_expect_tx(&bars[1], G::SLAB_LOAD_BYTES);
                 for (int ar = RPR; ar < RC; ++ar) bulk_load(slab + ar * SH, in_row(p, ar), G::ROW_BYTES, &bars[1]);
             }
-            // 1. n2-axis r2c: round 0 from the stage, then the rows in the slab
+            // 1. n2-axis r2c: wave 0 from the stage, then the rows in the slab
             wait(0, par);
             {
                 float2 v[ER];
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(NT, MINB) cplane_kernel(CPlaneArgs a)
                 float2* row = slab + rr * SH;
                 row_r2c_regs<LR, ER, SlabRowExchange>(v, row, true, tr, lane, row, a.tw_row, a.twpack);
             }
-            __syncthreads();  // stage consumed: prefetch the next plane's round 0
+            __syncthreads();  // stage consumed: prefetch the next plane's wave 0
             if (leader && p + ncl < a.planes) issue_stage(p + ncl);
             if (RC > RPR) wait(1, par);
 #pragma unroll 1
