@@ -259,6 +259,8 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     args.shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else (args.n, args.n, args.n)
+    if args.field == "spectrum" and args.shape[2] % 2:
+        args.field = "uniform"  # the spectrum-shaped field is defined for even n2 only
 
     if args.impl == "reference":
         run_reference(args)
