@@ -1,10 +1,13 @@
 """The C-ABI library builds for sm_103a, loads, and exports every function
 include/fft3d.h declares; host-side argument checks answer without a GPU."""
 import ctypes
+import os
 
 import pytest
 
 import paper_1406_5597_gb300 as fft3d
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -83,3 +86,32 @@ def test_null_handles(lib):
         fft3d.fft3d_get_plane_choice(None)
     buf = ctypes.create_string_buffer(8)
     assert lib.fft3d_describe(None, buf, 8) == fft3d.FFT3D_ERR_INVALID_ARG
+
+
+def test_binding_signatures_match_the_header():
+    """Every prototype in include/fft3d.h has a binding entry with the same
+    number of arguments and a matching return kind (void / int / size_t /
+    pointer), so no argument is marshalled into the wrong slot."""
+    import ctypes
+    import re
+    src = open(os.path.join(ROOT, "include", "fft3d.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    protos = re.findall(r"([A-Za-z_][\w\s\*]*?)\b(fft3d_\w+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S)
+    assert len(protos) >= 40
+    for ret, name, params in protos:
+        p = " ".join(params.split())
+        nargs = 0 if p in ("", "void") else len(p.split(","))
+        assert name in fft3d._SIGS, name
+        argtypes, restype = fft3d._SIGS[name]
+        assert len(argtypes) == nargs, (name, nargs, len(argtypes))
+        ret = " ".join(ret.split())
+        if ret == "void":
+            assert restype is None, name
+        elif ret == "int":
+            assert restype is ctypes.c_int, name
+        elif ret == "size_t":
+            assert restype is ctypes.c_size_t, name
+        elif ret == "double":
+            assert restype is ctypes.c_double, name
+        else:  # a handle or a string
+            assert restype in (ctypes.c_void_p, ctypes.c_char_p), (name, ret)
