@@ -47,7 +47,7 @@ def dist_env():
 def workload_config(n, args):
     n0, n1, n2 = args.shape
     field = ("spectrum-shaped velocity component (seed 1408)" if args.field == "spectrum"
-             else "seeded uniform[-1,1) field (torch generator, seed 1408)")
+             else "seeded uniform[-1,1) field (seed 1408)")
     return {
         "workload": f"{n0}x{n1}x{n2} FP32 r2c+c2r, transpose-free, {field}",
         "n0": n0, "n1": n1, "n2": n2, "batch": 1,
@@ -177,11 +177,6 @@ def clocks_rejected(clocks, world=1, device=None):
     return bad
 
 
-def make_field(n):
-    """Spectrum-shaped half spectrum S (complex64 numpy) of velocity component 0."""
-    return make_field_shape(n, n, n)
-
-
 def make_field_shape(n0, n1, n2):
     import numpy as np
 
@@ -191,37 +186,48 @@ def make_field_shape(n0, n1, n2):
 
 
 def run_reference(args):
-    """FP64 CPU oracle on the host cores, same workload, metric and unit."""
+    """FP64 CPU oracle on the host cores, same workload (shape and field),
+    metric and unit; W warm-up steps and K timed ones, both capped so that the
+    run stays within a few minutes."""
     rank, _, world = dist_env()
     if rank != 0:
         return
     import numpy as np
 
     import oracle
-    n = args.n
-    S = make_field(n)
-    x = oracle.c2r3d(S.astype(np.complex128), n)  # setup, not timed
-    nbytes, _, _ = two_pass_bytes(n, n, n)
+    import synth
+    n0, n1, n2 = args.shape
+    if args.field == "spectrum":
+        x = oracle.c2r3d(make_field_shape(n0, n1, n2).astype(np.complex128), n2)  # setup, not timed
+    else:
+        x = synth.uniform_field((n0, n1, n2), 1408)
+    nbytes, _, _ = two_pass_bytes(n0, n1, n2)
     cores = oracle.threads()
+
+    def step():
+        X = oracle.r2c3d(x)
+        oracle.c2r3d(X, n2)
+
     t0 = time.perf_counter()
-    X = oracle.r2c3d(x)
-    oracle.c2r3d(X, n)
+    step()
     t_first = time.perf_counter() - t0
+    warmup = 1 + max(0, min(args.warmup - 1, int(30.0 / max(t_first, 1e-3))))
+    for _ in range(warmup - 1):
+        step()
     steps = max(1, min(args.steps, int(150.0 / max(t_first, 1e-3))))
     times = []
     for _ in range(steps):
         t0 = time.perf_counter()
-        X = oracle.r2c3d(x)
-        oracle.c2r3d(X, n)
+        step()
         times.append(time.perf_counter() - t0)
     ms = 1e3 * statistics.mean(times)
     value = nbytes / (ms * 1e-3) / 1e9
-    sample = (f"full {n}^3 r2c+c2r in FP64 per step; {steps} timed step(s) after 1 warm-up "
-              f"(steps capped so the run stays within a few minutes)")
+    sample = (f"full {n0}x{n1}x{n2} r2c+c2r in FP64 per step; {steps} timed step(s) after {warmup} warm-up "
+              f"step(s) (both capped so the run stays within a few minutes)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": steps, "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(n, args),
+        "steps": steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(n0, args),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
