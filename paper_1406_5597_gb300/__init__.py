@@ -266,7 +266,18 @@ def fft3d_nonlinear_destroy(nl):
     load().fft3d_nonlinear_destroy(_v(nl))
 
 
-class NonlinearTerm:
+class _Closing:
+    """Releases the handle on leaving a with-block (close() is idempotent)."""
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+
+class NonlinearTerm(_Closing):
     """Owning wrapper of fft3d_nonlinear_*: workspace from torch, then
     __call__(uhat (3, n0, n1, H) complex64 CUDA) -> (6, n0, n1, H) complex64."""
 
@@ -348,7 +359,7 @@ def fft3d_ns_destroy(ns):
     load().fft3d_ns_destroy(_v(ns))
 
 
-class NavierStokes:
+class NavierStokes(_Closing):
     """Owning wrapper of fft3d_ns_*: workspace from torch, then
     step(uhat, nu, dt) advances the (3, n0, n1, n2/2+1) complex64 CUDA tensor
     uhat in place by one Heun step."""
@@ -429,7 +440,7 @@ def fft3d_group_destroy(group):
     load().fft3d_group_destroy(_v(group))
 
 
-class Group:
+class Group(_Closing):
     """Owning wrapper of a grouped plan: dims [(n0, n1, n2), ...], counts
     [fields, ...].  r2c / c2r take lists of torch CUDA tensors, one per group
     (group i: counts[i] contiguous fields)."""
@@ -476,7 +487,7 @@ def error_string(status: int) -> str:
 
 # --- torch helpers (memory and streams only) -----------------------------------
 
-class Plan:
+class Plan(_Closing):
     """Owning wrapper of a plan handle (and of the workspace it may need)."""
 
     def __init__(self, n0, n1, n2, dtype=FFT3D_F32, batch=1, flags=0):

@@ -115,3 +115,16 @@ def test_binding_signatures_match_the_header():
             assert restype is ctypes.c_double, name
         else:  # a handle or a string
             assert restype in (ctypes.c_void_p, ctypes.c_char_p), (name, ret)
+
+
+def test_binding_objects_close_on_leaving_a_with_block():
+    """Plan, Group, NonlinearTerm and NavierStokes release their handle at the
+    end of a with-block; close() is idempotent (checked on handle-less objects,
+    which needs no GPU)."""
+    for cls in (fft3d.Plan, fft3d.Group, fft3d.NonlinearTerm, fft3d.NavierStokes):
+        obj = object.__new__(cls)
+        obj.handle = None
+        with obj as o:
+            assert o is obj
+        obj.close()
+        assert obj.handle is None
