@@ -220,6 +220,26 @@ def test_spot_bins_and_points_match_full_oracle():
     assert np.max(np.abs(gotp - np.array([y[j] for j in js]))) < 1e-9
 
 
+def test_separable_spot_bins_match_full_oracle_and_direct_sums():
+    """r2c_bins_sep (axis-by-axis sums, one j2 pass per distinct k2) against
+    the full oracle and against the per-bin direct sums, on an odd-sized
+    field; bins on the DC and Nyquist planes, repeated k2 values, and chunks
+    that end inside the field."""
+    shape = (18, 10, 12)
+    x32 = synth.uniform_field(shape, seed=12).astype(np.float32)
+    X = oracle.r2c3d(x32.astype(np.float64))
+    ks = [(0, 0, 0), (3, 7, 2), (17, 9, 6), (12, 5, 2), (1, 0, 6), (9, 4, 5)]
+    got = oracle.r2c_bins_sep(x32, ks, chunk_rows=7)
+    ref = np.array([X[k] for k in ks])
+    assert np.max(np.abs(got - ref)) < 1e-11 * np.max(np.abs(ref))
+    assert np.max(np.abs(got - oracle.r2c_bins_f32(x32, ks))) < 1e-11 * np.max(np.abs(ref))
+    # a transposed index would pick another bin: every bin differs from its
+    # axis-swapped partner on this field
+    assert np.min(np.abs(got[1:] - np.array([X[k[1] % 18, k[0] % 10, k[2]] for k in ks[1:]]))) > 1e-3
+    with pytest.raises(ValueError):
+        oracle.r2c_bins_sep(x32, [(0, 0, 7)])
+
+
 def test_spectrum_as_oracle():
     """x = c2r(S) for a Hermitian-consistent S gives r2c(x) = N S exactly (up to
     FP64 rounding): the spectral_velocity field is such an S."""
