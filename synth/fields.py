@@ -111,7 +111,7 @@ def energy_shape(k: np.ndarray, k0: float = 4.0, kc: float = 8.0) -> np.ndarray:
 
 
 def spectral_velocity(n0: int, n1: int, n2: int, seed: int, components=(0, 1, 2),
-                      plane_chunk: int = 32) -> np.ndarray:
+                      plane_chunk: int = 32, workers: int = 1) -> np.ndarray:
     """Half-spectrum (n0, n1, n2/2+1) complex128 of each requested velocity
     component of a random-phase, divergence-free, 2/3-truncated field.
 
@@ -131,6 +131,10 @@ def spectral_velocity(n0: int, n1: int, n2: int, seed: int, components=(0, 1, 2)
          and k2 = n2/2, else 2): the unnormalised inverse transform of the
          field then has unit rms per component on average, and the common
          factor keeps k . u_hat = 0.
+
+    ``workers`` > 1 draws chunks of planes on that many threads; the chunks'
+    energies are summed in plane order, so the result is bit for bit the same
+    for every worker count.
     """
     if n2 % 2:
         raise ValueError("n2 must be even")
@@ -144,11 +148,13 @@ def spectral_velocity(n0: int, n1: int, n2: int, seed: int, components=(0, 1, 2)
     nmin = min(n0, n1, n2)
     comps = tuple(components)
     out = np.zeros((len(comps), n0, n1, H), dtype=np.complex128)
-    energy = np.zeros(3)
 
     w = np.full(H, 2.0)
     w[0] = w[H - 1] = 1.0
-    for a0 in range(0, n0, plane_chunk):
+
+    def chunk(a0):
+        """Draw planes [a0, a0 + plane_chunk) into out; their energy per component."""
+        energy = np.zeros(3)
         b0 = min(n0, a0 + plane_chunk)
         K0 = k0v[a0:b0, None, None]
         K1 = k1v[None, :, None]
@@ -159,7 +165,7 @@ def spectral_velocity(n0: int, n1: int, n2: int, seed: int, components=(0, 1, 2)
         # only the modes that survive steps 1 and 5 are drawn (the others are 0)
         idx = np.flatnonzero(~zero)
         if idx.size == 0:
-            continue
+            return energy
         kkf = kk.ravel()[idx] if kk.size == zero.size else np.broadcast_to(kk, zero.shape).ravel()[idx]
         i0, rest = np.divmod(idx, n1 * H)
         i1, i2 = np.divmod(rest, H)
@@ -182,6 +188,18 @@ def spectral_velocity(n0: int, n1: int, n2: int, seed: int, components=(0, 1, 2)
                 dst = out[comps.index(c), a0:b0].reshape(-1)
                 dst[idx] = uc
         del a, f
+        return energy
+
+    starts = range(0, n0, plane_chunk)
+    if workers > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=workers) as ex:
+            parts = list(ex.map(chunk, starts))
+    else:
+        parts = [chunk(a0) for a0 in starts]
+    energy = np.zeros(3)
+    for e in parts:  # plane order, whatever the worker count
+        energy += e
 
     # Hermitian consistency on the k2 = 0 plane (step 6).
     for i in range(len(comps)):

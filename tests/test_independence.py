@@ -47,7 +47,7 @@ def test_oracle_never_touches_the_product():
 def test_shared_generators_hold_no_transform():
     for f in _files("synth/*.py"):
         text = open(f, errors="replace").read()
-        assert not re.search(r"\bnp\.fft\b|numpy\.fft|\bscipy\.fft|import oracle|paper_1406_5597_gb300", text), f
+        assert not re.search(r"\bnp\.fft\b|numpy\.fft|\bscipy\.fft|\btorch\.fft|import oracle|paper_1406_5597_gb300", text), f
 
 
 def test_product_fails_loudly_without_its_library(monkeypatch, tmp_path):

@@ -54,3 +54,27 @@ def test_spectral_velocity_properties():
     assert np.argmax(e) + 1 == 4
     assert abs(synth.energy_shape(8.0 - 1e-9) - synth.energy_shape(8.0)) < 1e-6
     assert abs(e[10] / e[7] - (11 / 8) ** (-5 / 3)) < 1e-12
+
+
+def test_spectral_velocity_same_for_every_worker_count():
+    """Threaded drawing (large fields) gives the single-threaded result bit for bit."""
+    a = synth.spectral_velocity(40, 36, 30, seed=1409, plane_chunk=6)
+    b = synth.spectral_velocity(40, 36, 30, seed=1409, plane_chunk=6, workers=4)
+    assert np.array_equal(a, b)
+
+
+def test_device_generators_match_the_host_ones():
+    """synth.device (torch arrays, here on the CPU) draws the same fields as
+    synth.fields: the uniform field bit for bit, the spectrum-shaped field to
+    complex64 rounding, for every component and with ragged plane chunks."""
+    torch = __import__("pytest").importorskip("torch")
+    from synth import device as sd
+    u = sd.uniform_field((3, 5, 7, 11), 1409, device="cpu").numpy()
+    assert np.array_equal(u, synth.uniform_field((3, 5, 7, 11), 1409).astype(np.float32))
+    for shape, seed, comp in (((30, 18, 16), 1408, 0), ((32, 24, 20), 5, 2), ((12, 16, 10), 7, 1)):
+        a = synth.spectral_velocity(*shape, seed=seed, components=(comp,))[0]
+        b = sd.spectral_velocity(*shape, seed=seed, component=comp, device="cpu", plane_chunk=5).numpy()
+        assert b.dtype == np.complex64
+        assert np.max(np.abs(b - a)) <= 2.0 ** -23 * np.max(np.abs(a))
+        assert np.array_equal(b == 0, a == 0)
+    assert torch is not None
