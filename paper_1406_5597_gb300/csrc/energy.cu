@@ -30,15 +30,15 @@ __device__ __forceinline__ int shell_of(long long kk4)
     return (int)b;
 }
 
-// grid (blocks_per_entry, batch); partials: batch x blocks x (nbins + 1) doubles,
-// slot nbins holds the block's total.
+// grid (blocks_per_entry, batch entries of this launch); batch entry b0 + blockIdx.y;
+// partials: batch x blocks x (nbins + 1) doubles, slot nbins holds the block's total.
 __global__ void energy_partials_kernel(const float2* __restrict__ X, int n0, int n1, int n2, int nbins,
-                                       double* __restrict__ partials)
+                                       long long b0, double* __restrict__ partials)
 {
     extern __shared__ double hist[];  // nbins + 1
     const int H = n2 / 2 + 1;
     const long long rows = (long long)n0 * n1;
-    const long long b = blockIdx.y;
+    const long long b = b0 + blockIdx.y;
     const float2* Xb = X + b * rows * H;
     for (int i = threadIdx.x; i <= nbins; i += blockDim.x) hist[i] = 0.0;
     __syncthreads();
@@ -84,6 +84,8 @@ __global__ void energy_finalize_kernel(const double* __restrict__ partials, int 
     }
 }
 
+constexpr long long kMaxGridY = 65535;
+
 }  // namespace
 
 int energy_blocks_per_entry(long long rows)
@@ -108,10 +110,14 @@ cudaError_t launch_energy(const void* X, int n0, int n1, int n2, int batch, int 
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    energy_partials_kernel<<<dim3(blocks, batch), 256, smem, s>>>(reinterpret_cast<const float2*>(X), n0, n1, n2,
-                                                                  nbins, scratch);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    // batch entries in launches of at most 65535 (the grid's y limit)
+    for (long long b0 = 0; b0 < batch; b0 += kMaxGridY) {
+        const unsigned nb = (unsigned)(batch - b0 < kMaxGridY ? batch - b0 : kMaxGridY);
+        energy_partials_kernel<<<dim3(blocks, nb), 256, smem, s>>>(reinterpret_cast<const float2*>(X), n0, n1, n2,
+                                                                   nbins, b0, scratch);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     const long long n = (long long)batch * (nbins + 1);
     energy_finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(scratch, blocks, nbins, batch, total, shells);
     return cudaGetLastError();

@@ -8,9 +8,14 @@
 // It needs no plan (the diagnostics use no twiddle tables) and allocates
 // nothing: the block partials go to one file-scope device array of fixed
 // size, which every GPU that loads this library holds until the process
-// exits.  Its device address is fetched once per device (first call on that
-// device, with the device current) and cached.
-#include <mutex>
+// exits.  Host code cannot use the array's name as a device address, so
+// every call looks up its address on the current device
+// (cudaGetSymbolAddress, a host-side lookup).  The first call on a device is
+// its set-up: the lookup may load this library's device code there, so it
+// must not happen inside a stream capture.  Looking up again on later calls
+// keeps the address right after anything that recreates the device's
+// context (cudaDeviceReset).
+#include <cstdint>
 
 #include "energy.h"
 #include "fft3d.h"
@@ -19,28 +24,16 @@ namespace {
 
 // Scratch capacity in doubles: 2 MiB.
 constexpr size_t kNoallocScratchDoubles = size_t(1) << 18;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_energy_scratch[kNoallocScratchDoubles];
 
-std::mutex g_setup_mutex;
-double* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_energy_scratch on the current device (set-up on first use).
+// Device address of g_energy_scratch on the current device.
 cudaError_t scratch_for_current_device(double** out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_energy_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_energy_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<double*>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    *out = static_cast<double*>(p);
     return cudaSuccess;
 }
 

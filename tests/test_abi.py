@@ -128,3 +128,34 @@ def test_binding_objects_close_on_leaving_a_with_block():
             assert o is obj
         obj.close()
         assert obj.handle is None
+
+
+def _cuda_device_present():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+@pytest.mark.skipif(_cuda_device_present(),
+                    reason="host buffers stand in for device ones here; only run where nothing can launch")
+def test_noalloc_energy_rejects_calls_beyond_its_scratch(lib):
+    """fft3d_energy_noalloc checks the scratch a call needs against its fixed
+    2^18-double array before anything touches the device: 8 x 8 x 2 with
+    batch 4 and 8192 shells needs 4 * 8 * 8193 = 262176 doubles, 32 over.
+    The buffers are sized for the whole call, and on a machine without a GPU
+    a missing check could only fail (no device to launch on), never write."""
+    import numpy as np
+    spec = np.zeros(4 * 8 * 8 * 2 * 2 + 4, dtype=np.float32)
+    total = np.full(4, 7.0)
+    shells = np.full(4 * 8192, 7.0)
+    sp = spec.ctypes.data + (-spec.ctypes.data) % 16  # 16-byte aligned start
+    st = fft3d.fft3d_energy_noalloc(sp, 8, 8, 2, 4, total.ctypes.data, shells.ctypes.data, 8192, 0)
+    assert st == fft3d.FFT3D_ERR_UNSUPPORTED_SIZE
+    assert np.all(total == 7.0) and np.all(shells == 7.0)
+    # one entry less fits (3 * 8 * 8193 doubles): it passes the size check and
+    # fails only on the missing device
+    st = fft3d.fft3d_energy_noalloc(sp, 8, 8, 2, 3, total.ctypes.data, shells.ctypes.data, 8192, 0)
+    assert st == fft3d.FFT3D_ERR_CUDA
+    assert np.all(total == 7.0) and np.all(shells == 7.0)
