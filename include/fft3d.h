@@ -4,7 +4,7 @@
  *
  * Method: Chatterjee, Verma & Chaudhuri, "Transpose-free Fast Fourier
  * Transform for Turbulence Simulation", arXiv:1406.5597.  Sec. 2 defines the
- * operation (a real n0 x n1 x n2 array to the complex n0 x n1 x (n2/2+1) half
+ * operation (a real n0 x n1 x n2 array to the complex n0 x n1 x H half
  * spectrum and back); Sec. 2.1 gives the steps (a 2D r2c per n0-plane, then a
  * 1D c2c along n0; the inverse in reverse order); Sec. 2.2 replaces the
  * transpose of step 2 by transforming the n0 axis where it lies, at its
@@ -15,14 +15,17 @@
  * Conventions (the paper names FFTW's transforms, Sec. 3, and fixes neither
  * sign nor scaling; this library takes FFTW's):
  *   forward  X[k] = sum_j x[j] exp(-2 pi i (k0 j0/n0 + k1 j1/n1 + k2 j2/n2)),
- *            0 <= k2 <= n2/2;
- *   inverse  y[j] = sum_{k2=0}^{n2/2} c_k2 Re(sum_{k0,k1} Y[k] exp(+2 pi i (...))),
- *            c_k2 = 1 at k2 = 0 and k2 = n2/2, else 2; unnormalised, so
- *            c2r(r2c(x)) = n0*n1*n2 * x.  The imaginary parts of the k2 = 0
- *            and k2 = n2/2 bins, after the n0 and n1 passes, are ignored.
+ *            0 <= k2 < H, H = floor(n2/2) + 1;
+ *   inverse  y[j] = sum_{k2=0}^{H-1} c_k2 Re(sum_{k0,k1} Y[k] exp(+2 pi i (...))),
+ *            c_k2 = 1 at k2 = 0 and, for even n2 only, at the Nyquist bin
+ *            k2 = n2/2; c_k2 = 2 for every other bin (for odd n2 there is no
+ *            Nyquist bin, so every k2 >= 1 weighs 2); unnormalised, so
+ *            c2r(r2c(x)) = n0*n1*n2 * x.  The imaginary part of the k2 = 0
+ *            bin, and for even n2 of the k2 = n2/2 bin, after the n0 and n1
+ *            passes, is ignored.
  *
  * Layouts: real data batch x n0 x n1 x n2 contiguous float; complex data
- * batch x n0 x n1 x H (H = n2/2+1) contiguous interleaved float pairs
+ * batch x n0 x n1 x H (H = floor(n2/2) + 1) contiguous interleaved float pairs
  * (float2, torch.complex64).  C row-major, n2 fastest, batch outermost.
  * All data pointers are DEVICE pointers unless a comment says otherwise.
  *
@@ -362,7 +365,8 @@ void fft3d_ns_destroy(fft3d_ns_handle ns);
  * spec:   batch*n0*n1*H float2 (device), read only, laid out as fft3d_r2c
  *         writes it for a plan without EXPLICIT_TRANSPOSE.
  * total:  batch doubles (device) or NULL: sum over the half spectrum of
- *         c_k2 |X|^2 (c_k2 = 1 at k2 = 0 and k2 = n2/2, else 2), which equals
+ *         c_k2 |X|^2 (c_k2 = 1 at k2 = 0 and, for even n2, at k2 = n2/2;
+ *         else 2), which equals
  *         n0*n1*n2 * sum_j x_j^2 when spec = r2c(x) (Parseval).
  * shells: batch*nbins doubles (device) or NULL: the same sum per integer
  *         shell b = floor(|k| + 1/2) (shell 0 holds only k = 0; shell b >= 1
@@ -393,9 +397,12 @@ int fft3d_energy(fft3d_handle plan, const void* spec, double* total, double* she
  * it, B = min(256, ceil(n0*n1/8)); a larger call is rejected with
  * FFT3D_ERR_UNSUPPORTED_SIZE before anything is launched.
  *
- * The first call on a device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture.  Every call on a device shares the one array, and it keeps the
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, a host-side lookup, so the address stays right after
+ * anything that recreates the device's context, such as cudaDeviceReset).
+ * The first call on a device is its set-up: that lookup may load the
+ * library's device code there, so make the first call on each device before
+ * any stream capture.  Every call on a device shares the one array, and it keeps the
  * last call's contents (each call writes all the scratch it reads, so nothing
  * needs clearing): calls that overlap on the GPU, e.g. on two streams without
  * ordering between them, race and give wrong results; order them, for

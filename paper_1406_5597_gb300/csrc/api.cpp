@@ -14,6 +14,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <string>
 #include <utility>
@@ -427,6 +428,7 @@ struct fft3d_plan_s {
         CUtensorMap map;
     } maps[8];
     int next_map = 0;
+    std::mutex maps_mutex;  // guards maps / next_map (a plan may serve several host threads)
 };
 
 namespace {
@@ -513,22 +515,30 @@ bool tma_ok(const fft3d_plan_s* p, const Axis& a, long long S, long long C, long
     return tma_mode(p, a, S, C, Bs) != 0;
 }
 
-const CUtensorMap* tensor_map(fft3d_plan_s* p, const Axis& a, const ColArgs& ca, bool pair)
+// The tensor map of a column-pass operand, copied into *out (the cache is
+// shared by every host thread that uses the plan, so it is read and written
+// under the plan's lock, and the caller launches with its own copy).
+bool tensor_map(fft3d_plan_s* p, const Axis& a, const ColArgs& ca, bool pair, CUtensorMap* out)
 {
+    std::lock_guard<std::mutex> lock(p->maps_mutex);
     for (auto& m : p->maps)
-        if (m.base == ca.data && m.S == ca.S && m.C == ca.C && m.nb == ca.nb && m.pair == pair) return &m.map;
+        if (m.base == ca.data && m.S == ca.S && m.C == ca.C && m.nb == ca.nb && m.pair == pair) {
+            *out = m.map;
+            return true;
+        }
     auto& m = p->maps[p->next_map];
     p->next_map = (p->next_map + 1) % 8;
     if (col_tensor_map_host(&m.map, ca, a.L, a.spec->tma_W, pair) != cudaSuccess) {
         m.base = nullptr;
-        return nullptr;
+        return false;
     }
     m.base = ca.data;
     m.S = ca.S;
     m.C = ca.C;
     m.nb = ca.nb;
     m.pair = pair;
-    return &m.map;
+    *out = m.map;
+    return true;
 }
 
 // One column pass with full control of the arguments (destination, mask, scale).
@@ -546,9 +556,10 @@ cudaError_t launch_col_args(fft3d_plan_s* p, const Axis& a, int dir, const ColAr
     const bool n0axis = (&a == &p->ax0);
     const int mode = tma_mode(p, a, ca.S, ca.C, ca.Bs);
     if ((n0axis ? p->choice_tma : p->choice_tma1) && mode) {
-        if (const CUtensorMap* m = tensor_map(p, a, ca, mode == 2)) {
-            if (mode == 2) return dir < 0 ? a.spec->tma_pair_fwd(ca, *m, s) : a.spec->tma_pair_inv(ca, *m, s);
-            return dir < 0 ? a.spec->tma_fwd(ca, *m, s) : a.spec->tma_inv(ca, *m, s);
+        CUtensorMap m;
+        if (tensor_map(p, a, ca, mode == 2, &m)) {
+            if (mode == 2) return dir < 0 ? a.spec->tma_pair_fwd(ca, m, s) : a.spec->tma_pair_inv(ca, m, s);
+            return dir < 0 ? a.spec->tma_fwd(ca, m, s) : a.spec->tma_inv(ca, m, s);
         }
     }
     const int w = n0axis ? p->choice_w0 : p->choice_w1;

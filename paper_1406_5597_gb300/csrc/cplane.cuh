@@ -351,7 +351,7 @@ inline cudaError_t launch_cplane(const CPlaneArgs& a, cudaStream_t s)
     using G = CPlaneGeom<LR, ER, LC, C, NT>;
     constexpr size_t smem = DIR < 0 ? G::smem_fwd : G::smem_inv;
     auto k = cplane_kernel<LR, ER, LC, C, NT, DIR, MINB>;
-    static int max_clusters = 0;  // co-resident clusters, queried once per instantiation
+    static PerDevice resident;  // co-resident clusters, queried once per device
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -363,18 +363,18 @@ inline cudaError_t launch_cplane(const CPlaneArgs& a, cudaStream_t s)
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (max_clusters == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+    int max_clusters = 0;
+    cudaError_t e = per_device(resident, &max_clusters, [&](int, int* v) {
+        cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (r != cudaSuccess) return r;
         if (C > 8) {
-            e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            if (e != cudaSuccess) return e;
+            r = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (r != cudaSuccess) return r;
         }
         cfg.gridDim = dim3(C * 64);
-        e = cudaOccupancyMaxActiveClusters(&max_clusters, k, &cfg);
-        if (e != cudaSuccess) return e;
-        if (max_clusters < 1) return cudaErrorInvalidConfiguration;
-    }
+        return cudaOccupancyMaxActiveClusters(v, k, &cfg);
+    });
+    if (e != cudaSuccess) return e;
     if (a.planes <= 0) return cudaSuccess;
     const long long ncl = a.planes < max_clusters ? a.planes : max_clusters;
     cfg.gridDim = dim3((unsigned)(ncl * C));

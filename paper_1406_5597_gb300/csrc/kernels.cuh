@@ -22,6 +22,7 @@
 #include <cstdint>
 
 #include "args.h"
+#include "launch_cache.h"
 #include "stockham.cuh"
 #include "tma.cuh"
 
@@ -684,11 +685,10 @@ inline cudaError_t launch_col(const ColArgs& a, int w, cudaStream_t s)
     const size_t smem_max = (size_t)L * W * sizeof(float2);
     const size_t smem = (size_t)L * wr * sizeof(float2);
     auto k = col_kernel<L, E, DIR, MAXT>;
-    static bool attr_set = false;  // one attribute call per instantiation (per process)
-    if (smem_max > 48 * 1024 && !attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    static PerDevice limit;  // the shared memory limit, raised once per device
+    if (smem_max > 48 * 1024) {
+        cudaError_t e = smem_limit_per_device(limit, k, smem_max);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     const long long tiles = a.nb * ((a.C + wr - 1) / wr);
     if (tiles <= 0) return cudaSuccess;
@@ -739,11 +739,10 @@ inline cudaError_t launch_row_warp(const RowArgs& a, int rows, cudaStream_t s)
     const long long blocks = (a.rows + rr - 1) / rr;
     if (blocks <= 0) return cudaSuccess;
     auto k = (DIR < 0) ? row_r2c_warp_kernel<L, E, ROWS> : row_c2r_warp_kernel<L, E, ROWS>;
-    static bool attr_set = false;
-    if (smem_max > 48 * 1024 && !attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    static PerDevice limit;  // the shared memory limit, raised once per device
+    if (smem_max > 48 * 1024) {
+        cudaError_t e = smem_limit_per_device(limit, k, smem_max);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     k<<<(unsigned)blocks, dim3(T, rr), smem, s>>>(a);
     return cudaGetLastError();
@@ -755,21 +754,13 @@ inline cudaError_t launch_col_pipe(const ColArgs& a, cudaStream_t s)
     constexpr int T = L / E;
     const size_t smem = (size_t)(STAGES + 1) * L * W * sizeof(float2);
     auto k = col_pipe_kernel<L, E, DIR, W, STAGES>;
-    static int grid_per_sm = 0;  // resident CTAs per SM, queried once per instantiation
-    static int sms = 0;
-    if (grid_per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&grid_per_sm, k, W * T, smem);
-        if (e != cudaSuccess) return e;
-        if (grid_per_sm < 1) return cudaErrorInvalidConfiguration;
-    }
+    static PerDevice resident;  // resident CTAs on the device, queried once per device
+    int ctas = 0;
+    cudaError_t e = resident_ctas_per_device(resident, k, W * T, smem, &ctas);
+    if (e != cudaSuccess) return e;
     const long long ntiles = a.nb * ((a.C + W - 1) / W);
     if (ntiles <= 0) return cudaSuccess;
-    long long grid = (long long)grid_per_sm * sms;
+    long long grid = ctas;
     if (grid > ntiles) grid = ntiles;
     k<<<(unsigned)grid, dim3(W, T), smem, s>>>(a, ntiles);
     return cudaGetLastError();
@@ -784,21 +775,13 @@ inline cudaError_t launch_col_tma(const ColArgs& a, const CUtensorMap& map, cuda
     const size_t smem = (size_t)STAGES * L * WS * sizeof(float2) + (XB ? (size_t)L * W * sizeof(float2) : 0) +
                         STAGES * sizeof(unsigned long long);
     auto k = col_tma_kernel<L, E, DIR, W, STAGES, PF, PAIR>;
-    static int per_sm = 0;
-    static int sms = 0;
-    if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, W * T, smem);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    }
+    static PerDevice resident;  // resident CTAs on the device, queried once per device
+    int ctas = 0;
+    cudaError_t e = resident_ctas_per_device(resident, k, W * T, smem, &ctas);
+    if (e != cudaSuccess) return e;
     const long long ntiles = a.nb * ((a.C + W - 1) / W);
     if (ntiles <= 0) return cudaSuccess;
-    long long grid = (long long)per_sm * sms;
+    long long grid = ctas;
     if (grid > ntiles) grid = ntiles;
     k<<<(unsigned)grid, dim3(W, T), smem, s>>>(map, a, ntiles);
     return cudaGetLastError();

@@ -3,6 +3,7 @@
 // projection, viscous term and the Heun update, one pass over the half
 // spectrum per stage.  Each thread takes bins i, i + stride, ...; the bin's
 // signed wavenumbers come from its flat index.
+#include "launch_cache.h"
 #include "ns.h"
 
 namespace fft3d {
@@ -74,13 +75,13 @@ __global__ void __launch_bounds__(256) ns_stage_kernel(NsArgs a)
 cudaError_t launch_ns_stage(const NsArgs& a, int stage, cudaStream_t s)
 {
     if (a.M <= 0) return cudaSuccess;
-    static int blocks = 0;  // a few CTAs per SM, grid-stride over the bins
-    if (blocks == 0) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        blocks = 8 * (sms > 0 ? sms : 1);
-    }
+    static PerDevice sm_count;  // a few CTAs per SM, grid-stride over the bins
+    int sms = 0;
+    if (per_device(sm_count, &sms, [](int dev, int* v) {
+            return cudaDeviceGetAttribute(v, cudaDevAttrMultiProcessorCount, dev);
+        }) != cudaSuccess)
+        sms = 1;
+    const long long blocks = 8ll * sms;
     long long need = (a.M + 255) / 256;
     const unsigned grid = (unsigned)(need < blocks ? need : blocks);
     if (stage == 1) ns_stage_kernel<1><<<grid, 256, 0, s>>>(a);

@@ -150,27 +150,20 @@ inline cudaError_t launch_plane(const PlaneArgs& a, cudaStream_t s)
     constexpr int TR = LR / ER, RPI = NT / TR, TC = LC / EC, WC = NT / TC;
     const size_t smem = PlaneSmem<LR>::bytes(RPI, LC, WC);
     auto k = plane_kernel<LR, ER, LC, EC, NT, DIR, MINB>;
-    static int per_sm = 0, sms = 0;
-    if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    }
+    static PerDevice resident;  // resident CTAs on the device, queried once per device
+    int ctas = 0;
+    cudaError_t e = resident_ctas_per_device(resident, k, NT, smem, &ctas);
+    if (e != cudaSuccess) return e;
     const int RI = (LC + RPI - 1) / RPI, CI = (a.H + WC - 1) / WC;
     const int Z = RI + CI;
     // The resident CTAs span about grid/Z slots of the item order at any time;
     // the consumers must trail the producers by more than that, or they wait.
     PlaneArgs b = a;
-    const long long span = ((long long)per_sm * sms + Z - 1) / Z;
+    const long long span = ((long long)ctas + Z - 1) / Z;
     b.lag = (int)(span + a.lag);
     if (b.ring_planes <= 2 * b.lag) b.ring_planes = 0;  // ring too short to trail the consumers: work in place
     const long long nitems = (b.planes + b.lag) * (long long)Z;
-    long long grid = (long long)per_sm * sms;
+    long long grid = ctas;
     if (grid > nitems) grid = nitems;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);

@@ -23,6 +23,7 @@
 #include <cuda_fp16.h>
 #include <cstdint>
 
+#include "launch_cache.h"
 #include "stockham.cuh"
 #include "tma.cuh"
 
@@ -341,12 +342,9 @@ inline cudaError_t launch_col_tc(const ColArgs& a, const uint16_t* gtab, cudaStr
     constexpr int T = L / 16;
     const size_t smem = col_tc_smem<L, DIR, MODE, W>();
     auto k = col_tc_kernel<L, DIR, MODE, W>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static PerDevice limit;  // the shared memory limit, raised once per device
+    cudaError_t e = smem_limit_per_device(limit, k, smem);
+    if (e != cudaSuccess) return e;
     const long long tiles = a.nb * ((a.C + W - 1) / W);
     if (tiles <= 0) return cudaSuccess;
     k<<<(unsigned)tiles, dim3(W, T), smem, s>>>(a, gtab);
