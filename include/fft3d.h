@@ -230,14 +230,17 @@ double fft3d_pass_bytes(fft3d_handle plan, int pass);
 
 /*
  * Autotuning.  A plan's kernel shapes (columns per CTA of the n0 and n1
- * column kernels, rows per CTA of the row kernels, TMA-fed or plain kernel for
- * the n0 and the n1 pass) start at compiled defaults; fft3d_autotune times
- * each pass's candidates on the caller's buffers (real: batch*N floats, cplx:
+ * column kernels, rows per CTA of the row kernels, and the kernel form of the
+ * n0 and the n1 pass) start at compiled defaults; fft3d_autotune times each
+ * pass's candidates on the caller's buffers (real: batch*N floats, cplx:
  * batch*M float2; both device, contents destroyed) with CUDA events, reps
  * timed runs per candidate, and keeps the fastest.  Synchronises stream.  The
- * choices are five ints {w0, w1, rows, tma0, tma1} (widths/rows 0 = compiled
- * default; tma flags 0/1) that fft3d_get_choices / fft3d_set_choices read and
- * write (host array), so a caller can cache them per GPU and shape.
+ * choices are five ints {w0, w1, rows, form0, form1} (widths/rows 0 = compiled
+ * default; forms: 0 plain one-tile-per-CTA kernel, 1 TMA-fed persistent
+ * kernel, 2 and 3 the first and second cluster-split kernel compiled for that
+ * axis length, where one exists) that fft3d_get_choices / fft3d_set_choices
+ * read and write (host array), so a caller can cache them per GPU and shape;
+ * fft3d_set_choices rejects a form the axis does not have.
  * FFT3D_F64 plans have nothing to tune: FFT3D_ERR_INVALID_ARG.
  */
 int fft3d_autotune(fft3d_handle plan, float* real, void* cplx, int reps, void* stream);

@@ -180,6 +180,7 @@ struct Axis {
     int L = 1;
     const LenEntry* spec = nullptr;
     const TcEntry* tc = nullptr;  // tensor-core radix-16 column kernel (TC dtypes)
+    const SplitEntry* split[2] = {nullptr, nullptr};  // cluster-split column kernels of this length
     GenPlan gen{};
     float2* d_tw = nullptr;
     float2* d_blu = nullptr;  // Bluestein tables (chirp, bhat, W_M), lengths with a prime factor above 7
@@ -338,6 +339,15 @@ cudaError_t setup_axis64(Axis& a)
     a.gen64.bhat = a.d_blu64 + L;
     a.gen64.twm = a.d_blu64 + L + M;
     return cudaSuccess;
+}
+
+// The cluster-split column kernels of length L (at most two, in table order).
+void find_split(int L, const SplitEntry* (&out)[2])
+{
+    int n = 0, k = 0;
+    const SplitEntry* e = split_entries(&n);
+    for (int i = 0; i < n && k < 2; ++i)
+        if (e[i].L == L) out[k++] = &e[i];
 }
 
 const TcEntry* find_tc(int L)
@@ -541,6 +551,13 @@ bool tensor_map(fft3d_plan_s* p, const Axis& a, const ColArgs& ca, bool pair, CU
     return true;
 }
 
+// The cluster-split kernel the plan's choice selects for this column axis, or nullptr.
+const SplitEntry* split_choice(const fft3d_plan_s* p, const Axis& a)
+{
+    const int form = (&a == &p->ax0) ? p->choice_tma : p->choice_tma1;
+    return form >= 2 ? a.split[form - 2] : nullptr;
+}
+
 // One column pass with full control of the arguments (destination, mask, scale).
 cudaError_t launch_col_args(fft3d_plan_s* p, const Axis& a, int dir, const ColArgs& ca, cudaStream_t s)
 {
@@ -554,8 +571,13 @@ cudaError_t launch_col_args(fft3d_plan_s* p, const Axis& a, int dir, const ColAr
     }
     if (uses_generic(p, a, false)) return generic_col(ca, a.gen, dir, s);
     const bool n0axis = (&a == &p->ax0);
+    const int form = n0axis ? p->choice_tma : p->choice_tma1;
+    if (form >= 2 && a.split[form - 2]) {  // cluster-split kernel
+        const SplitEntry* se = a.split[form - 2];
+        return dir < 0 ? se->fwd(ca, 0, s) : se->inv(ca, 0, s);
+    }
     const int mode = tma_mode(p, a, ca.S, ca.C, ca.Bs);
-    if ((n0axis ? p->choice_tma : p->choice_tma1) && mode) {
+    if (form == 1 && mode) {
         CUtensorMap m;
         if (tensor_map(p, a, ca, mode == 2, &m)) {
             if (mode == 2) return dir < 0 ? a.spec->tma_pair_fwd(ca, m, s) : a.spec->tma_pair_inv(ca, m, s);
@@ -613,9 +635,11 @@ std::string axis_desc(const fft3d_plan_s* p, const Axis& a, bool row)
                            : a.spec->row_rows;
         std::snprintf(b, sizeof b, "L=%d E=%d rows/CTA=%d %s", a.L, a.spec->row_E, rr,
                       a.spec->row_warp ? "warp" : "smem");
-    } else if (const int mode = (&a == &p->ax0) ? (p->choice_tma ? tma_mode(p, a, p->P, p->P, p->M) : 0)
-                                                : (p->choice_tma1 ? tma_mode(p, a, p->H, p->H, (long long)p->n1 * p->H)
-                                                                  : 0)) {
+    } else if (const SplitEntry* se = split_choice(p, a)) {
+        std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d cluster-split C=%d", a.L, se->E, se->W, se->C);
+    } else if (const int mode = (&a == &p->ax0) ? (p->choice_tma == 1 ? tma_mode(p, a, p->P, p->P, p->M) : 0)
+                                                : (p->choice_tma1 == 1 ? tma_mode(p, a, p->H, p->H, (long long)p->n1 * p->H)
+                                                                       : 0)) {
         std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d %s", a.L, mode == 2 ? a.spec->tma_pair_E : a.spec->tma_E,
                       a.spec->tma_W, mode == 2 ? "tma-row-pairs" : "tma");
     } else {
@@ -810,6 +834,7 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
         // odd rows and the FP64 path: the runtime-length kernels
         a.spec = ((i == 2 && (n2 & 1)) || dtype == FFT3D_F64) ? nullptr : find_len(a.L);
         a.tc = (is_tc_dtype(dtype) && i < 2) ? find_tc(a.L) : nullptr;
+        if (a.spec && i < 2) find_split(a.L, a.split);
         a.gen = generic_radices(a.L);
         if (upload(forward_table(a.L, a.L), &a.d_tw) != cudaSuccess ||
             (!smooth2357(a.L) && setup_bluestein(a) != cudaSuccess) ||
@@ -1447,7 +1472,9 @@ int fft3d_get_choices(fft3d_handle p, int* c)
 
 int fft3d_set_choices(fft3d_handle p, const int* c)
 {
-    if (!p || !c || c[0] < 0 || c[1] < 0 || c[2] < 0 || (c[3] != 0 && c[3] != 1) || (c[4] != 0 && c[4] != 1))
+    // column forms: 0 plain, 1 TMA ring, 2 + i the axis's i-th cluster-split kernel (must exist)
+    auto form_ok = [](int f, const Axis& a) { return f == 0 || f == 1 || ((f == 2 || f == 3) && a.split[f - 2]); };
+    if (!p || !c || c[0] < 0 || c[1] < 0 || c[2] < 0 || !form_ok(c[3], p->ax0) || !form_ok(c[4], p->ax1))
         return fail(FFT3D_ERR_INVALID_ARG);
     p->choice_w0 = c[0];
     p->choice_w1 = c[1];
@@ -1517,6 +1544,12 @@ int fft3d_autotune(fft3d_handle p, float* real, void* cplx, int reps, void* stre
             if (t < best) best = t, pick = w, pick_tma = 0;
         }
         p->choice_w1 = pick;
+        for (int i = 0; i < 2; ++i) {  // cluster-split kernels
+            if (!p->ax1.split[i]) continue;
+            p->choice_tma1 = 2 + i;
+            const float t = time_pass([&] { run_col(p, p->ax1, -1, X, H, H, B * n0, n1 * H, s); }, reps, s);
+            if (t < best) best = t, pick_tma = 2 + i;
+        }
         p->choice_tma1 = pick_tma;
     }
     // n0 pass: the TMA kernel or the plain kernel at several widths
@@ -1535,6 +1568,12 @@ int fft3d_autotune(fft3d_handle p, float* real, void* cplx, int reps, void* stre
             if (t < best) best = t, pick_w = w, pick_tma = 0;
         }
         p->choice_w0 = pick_w;
+        for (int i = 0; i < 2; ++i) {  // cluster-split kernels
+            if (!p->ax0.split[i]) continue;
+            p->choice_tma = 2 + i;
+            const float t = time_pass([&] { run_col(p, p->ax0, -1, X, p->P, p->P, B, p->M, s); }, reps, s);
+            if (t < best) best = t, pick_tma = 2 + i;
+        }
         p->choice_tma = pick_tma;
     }
     // plane form: separate row and n1 passes, or a cluster plane kernel of

@@ -147,6 +147,14 @@ struct TcEntry {
 };
 const TcEntry* tc_entries(int* n);
 
+// Column kernels of a long axis split over a thread-block cluster of C CTAs
+// (colsplit.cuh): E elements per thread, W columns per tile.
+struct SplitEntry {
+    int L, C, E, W;
+    ColFn fwd, inv;
+};
+const SplitEntry* split_entries(int* n);
+
 // Generic kernels: dir = -1 forward, +1 inverse.
 cudaError_t generic_col(const ColArgs& a, const GenPlan& g, int dir, cudaStream_t s);
 cudaError_t generic_row(const RowArgs& a, const GenPlan& g, int dir, cudaStream_t s);

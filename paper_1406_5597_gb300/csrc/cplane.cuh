@@ -30,54 +30,12 @@
 // barriers that every thread of the cluster reaches on every plane; the
 // kernel has no spin-waits).
 #pragma once
+#include "cluster.cuh"
 #include "cplane.h"
 #include "kernels.cuh"
 #include "tma.cuh"
 
 namespace fft3d {
-
-__device__ __forceinline__ unsigned cluster_ctarank()
-{
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ unsigned cluster_index()
-{
-    unsigned r;
-    asm volatile("mov.u32 %0, %%clusterid.x;\n" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ unsigned cluster_count()
-{
-    unsigned r;
-    asm volatile("mov.u32 %0, %%nclusterid.x;\n" : "=r"(r));
-    return r;
-}
-// Cluster-wide barrier: release the caller's shared / distributed shared
-// memory writes, acquire everybody else's.
-__device__ __forceinline__ void cluster_sync_all()
-{
-    asm volatile("barrier.cluster.arrive.release;\n" ::: "memory");
-    asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
-}
-// Address, in the cluster's shared window, of the same shared variable in CTA `rank`.
-__device__ __forceinline__ unsigned dsmem_map(const void* p, unsigned rank)
-{
-    unsigned r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ float2 dsmem_ld(unsigned addr)
-{
-    float2 v;
-    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
-    return v;
-}
-__device__ __forceinline__ void dsmem_st(unsigned addr, float2 v)
-{
-    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};\n" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
-}
 
 // Row transform exchange inside the row's own slab row (the row's values are
 // in registers by then): position p at p + p/32, which stays inside a padded

@@ -91,10 +91,21 @@ CASES = [
     ((256, 24, 20), 1, "bf16x3", "none"),
     ((11, 13, 22), 2, "f64", "none"),
     ((48, 80, 96), 1, "f64", "none"),
+    ((2048, 3, 4), 2, "f32", "split0"),         # cluster-split n0 pass, 2 CTAs, ragged tile
+    ((2048, 3, 4), 1, "f32", "split1"),         # 4 CTAs per cluster
+    ((1024, 3, 10), 1, "f32", "split1"),
+    ((1536, 4, 12), 1, "f32", "split0"),
+    ((2, 2048, 32), 1, "f32", "split0_n1"),     # the n1 pass, odd H
 ]
 
 
+# column-form choices {w0, w1, rows, form0, form1} of the split cases
+SPLIT_CHOICES = {"split0": [0, 0, 0, 2, 0], "split1": [0, 0, 0, 3, 0], "split0_n1": [0, 0, 0, 0, 2]}
+
+
 def _flags(lib, name):
+    if name in SPLIT_CHOICES:
+        return 0
     return {"none": 0, "padded": lib.FFT3D_FLAG_PADDED_REAL, "preserve": lib.FFT3D_FLAG_PRESERVE_INPUT,
             "transpose": lib.FFT3D_FLAG_EXPLICIT_TRANSPOSE,
             "transpose_back": lib.FFT3D_FLAG_EXPLICIT_TRANSPOSE | lib.FFT3D_FLAG_TRANSPOSE_BACK,
@@ -113,6 +124,9 @@ def test_no_write_outside_the_operands(cuda_lib, shape, batch, dt, fl):
     dtype = {"f32": lib.FFT3D_F32, "bf16x3": lib.FFT3D_F32_TC_BF16X3, "f64": lib.FFT3D_F64}[dt]
     flags = _flags(lib, fl)
     plan = lib.Plan(n0, n1, n2, dtype=dtype, batch=batch, flags=flags)
+    if fl in SPLIT_CHOICES:
+        assert lib.fft3d_set_choices(plan.handle, SPLIT_CHOICES[fl]) == lib.FFT3D_OK
+        assert "cluster-split" in plan.describe()
     rt = torch.float64 if f64 else torch.float32
     ct = torch.complex128 if f64 else torch.complex64
     row = 2 * H if fl == "padded" else n2

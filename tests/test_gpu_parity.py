@@ -750,6 +750,51 @@ def test_long_axis_column_forms_match_oracle(cuda_lib, shape):
     plan.close()
 
 
+@pytest.mark.parametrize("shape,batch", [((2048, 2, 6), 1), ((1024, 3, 10), 1), ((1536, 4, 12), 1),
+                                         ((2, 2048, 32), 1), ((3, 1024, 30), 1), ((1024, 2, 8), 2),
+                                         ((2048, 3, 4), 2)],
+                         ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else f"b{v}")
+def test_cluster_split_column_forms_match_oracle(cuda_lib, shape, batch):
+    """The cluster-split column kernels (forms 2 and 3 of the n0 and n1
+    passes: the tile's rows split by residue over a 2- or 4-CTA cluster, the
+    final radix-C step through distributed shared memory) give the oracle's
+    transform in both directions: ragged column tiles, batches, the n1 axis,
+    and the input-preserving inverse (its first pass writes elsewhere)."""
+    lib = cuda_lib
+    n0, n1, n2 = shape
+    H = n2 // 2 + 1
+    lead = (batch,) if batch > 1 else ()
+    x32 = synth.uniform_field(lead + shape, seed=61).astype(np.float32)
+    ref = oracle.r2c3d(x32.astype(np.float64))
+    Y64 = random_half_spectrum((batch * n0, n1, H), 63).reshape(lead + (n0, n1, H))
+    yref = oracle.c2r3d(Y64.astype(np.complex128), n2)
+    xd = torch.from_numpy(x32).cuda()
+    tried = 0
+    for flags in (0, lib.FFT3D_FLAG_PRESERVE_INPUT):
+        plan = lib.Plan(n0, n1, n2, lib.FFT3D_F32, batch, flags)
+        for f0 in (0, 2, 3):
+            for f1 in (0, 2, 3):
+                if f0 < 2 and f1 < 2:
+                    continue
+                if lib.fft3d_set_choices(plan.handle, [0, 0, 0, f0, f1]) != lib.FFT3D_OK:
+                    continue  # no such form on this axis
+                tried += 1
+                assert "cluster-split" in plan.describe()
+                X = torch.empty(lead + (n0, n1, H), dtype=torch.complex64, device="cuda")
+                plan.r2c(xd.data_ptr(), X.data_ptr())
+                torch.cuda.synchronize()
+                assert rel_l2(X.cpu().numpy(), ref) <= TOL, (f0, f1, flags)
+                Yd = torch.from_numpy(Y64).cuda()
+                y = torch.empty_like(xd)
+                plan.c2r(Yd.data_ptr(), y.data_ptr())
+                torch.cuda.synchronize()
+                assert rel_l2(y.cpu().numpy(), yref) <= TOL, (f0, f1, flags)
+                if flags:
+                    assert np.array_equal(Yd.cpu().numpy(), Y64)  # the input survived
+        plan.close()
+    assert tried >= 2
+
+
 # ---------------------------------------------------------------------------
 # FP64 path (FFT3D_F64): every pass on the FP64 runtime-length kernels.
 # ---------------------------------------------------------------------------
