@@ -32,7 +32,7 @@ import oracle
 import synth
 from synth import device as synth_device
 from synth.device import uniform_field as device_uniform
-from tests.errmodel import spot_bound, spot_report
+from tests.errmodel import line_rms, spot_bound, spot_report
 
 pytestmark = pytest.mark.gpu
 
@@ -165,9 +165,10 @@ def _check_shape(lib, shape, dtypes, seed=1409):
         torch.cuda.synchronize()
         got = np.array([X[tuple(k)].item() for k in ks])
         rms = (_sum_sq(X) / X.numel()) ** 0.5
-        rep = spot_report(got, ref, rms, dt)
+        lines = line_rms(X, ks)
+        rep = spot_report(got, ref, rms, dt, lines, max(shape))
         print(f"\n{shape} {NAMES[dt]} spot bins: {rep}")
-        assert np.all(np.abs(got - ref) <= spot_bound(ref, rms, dt)), (dt, rep)
+        assert np.all(np.abs(got - ref) <= spot_bound(ref, rms, dt, lines, max(shape))), (dt, rep)
         if dt == 0:
             total, _ = plan.energy(X, 4)
             assert abs(total.item() / N - sumsq) <= 1e-5 * sumsq

@@ -14,7 +14,7 @@ import torch
 
 import oracle
 import synth
-from tests.errmodel import spot_bound, spot_report
+from tests.errmodel import line_rms, spot_bound, spot_report
 
 pytestmark = pytest.mark.gpu
 
@@ -950,9 +950,11 @@ def test_512_spectrum_as_oracle_and_spot_bins(cuda_lib, field512, flags):
     ref = oracle.r2c_bins_f32(x32, ks)
     got = np.array([X[tuple(k)] for k in ks])
     # per-bin bound of the FP32 error model (tests/errmodel.py): the spread
-    # part scales with the field's rms, the local part with the bin
+    # part scales with the field's rms, the line part with the axis lines
+    # through the bin, the local part with the bin
     rms = np.sqrt(np.mean(np.abs(X) ** 2))
-    assert np.all(np.abs(got - ref) <= spot_bound(ref, rms)), spot_report(got, ref, rms)
+    lines = line_rms(X, ks)
+    assert np.all(np.abs(got - ref) <= spot_bound(ref, rms, 0, lines, n)), spot_report(got, ref, rms, 0, lines, n)
 
 
 def test_512_inverse(cuda_lib, field512):
@@ -967,4 +969,5 @@ def test_512_inverse(cuda_lib, field512):
     ref = oracle.c2r_points_c64(Y, n, js)
     got = np.array([y[tuple(j)] for j in js])
     rms = np.sqrt(np.mean(y ** 2))
-    assert np.all(np.abs(got - ref) <= spot_bound(ref, rms)), spot_report(got, ref, rms)
+    lines = line_rms(y, js)
+    assert np.all(np.abs(got - ref) <= spot_bound(ref, rms, 0, lines, n)), spot_report(got, ref, rms, 0, lines, n)
