@@ -29,14 +29,21 @@
  * (float2, torch.complex64).  C row-major, n2 fastest, batch outermost.
  * All data pointers are DEVICE pointers unless a comment says otherwise.
  *
- * Ownership: the caller owns every data buffer.  A plan owns only its small
+ * Ownership: the caller owns every data buffer.  A plan owns its small
  * twiddle tables and a device status word (allocated at plan time, freed by
- * fft3d_destroy).  Large workspace, where a variant needs it, is lent by the
- * caller through fft3d_set_workspace.
+ * fft3d_destroy); an FP32 plan whose n0 axis is 1024, 1536 or 2048 long
+ * (and n1*(n2/2+1) even) also owns the scratch of the residue-split n0
+ * kernel (column form 5): (C - 1) x 64 KB per SM for L = 512 C, 10 to 30 MB.
+ * Large workspace, where a variant needs it, is lent by the caller through
+ * fft3d_set_workspace.
  *
  * Streams: every launch goes on the stream passed in (a cudaStream_t given
  * as void*; NULL means the legacy default stream).  Nothing synchronises
  * implicitly except fft3d_plan*, fft3d_destroy and fft3d_query_device_status.
+ * Calls on one plan from several host threads or streams may overlap (its
+ * host-side caches are locked) unless the plan uses memory shared between
+ * calls: the scratch of column form 5 or a caller workspace.  Such calls must
+ * be ordered on the GPU (for instance, issued on one stream).
  *
  * Errors: functions returning int return an fft3d_status.  Argument errors
  * are found before any launch and leave the output untouched.  The status of
@@ -238,7 +245,12 @@ double fft3d_pass_bytes(fft3d_handle plan, int pass);
  * choices are five ints {w0, w1, rows, form0, form1} (widths/rows 0 = compiled
  * default; forms: 0 plain one-tile-per-CTA kernel, 1 TMA-fed persistent
  * kernel, 2 and 3 the first and second cluster-split kernel compiled for that
- * axis length, where one exists) that fft3d_get_choices / fft3d_set_choices
+ * axis length, 4 the TMA-fed cluster split (lengths 1024, 1536, 2048: 512-row
+ * TMA sub-transforms on 2, 3 or 4 CTAs; it needs an even axis stride of at
+ * least 16 complex values and otherwise runs as form 0), 5 (n0 pass only)
+ * the residue split through L2 (same lengths and condition: one CTA per tile,
+ * the 512-row residues parked in plan-owned scratch), where one exists)
+ * that fft3d_get_choices / fft3d_set_choices
  * read and write (host array), so a caller can cache them per GPU and shape;
  * fft3d_set_choices rejects a form the axis does not have.
  * FFT3D_F64 plans have nothing to tune: FFT3D_ERR_INVALID_ARG.
@@ -269,20 +281,46 @@ int fft3d_set_plane_choice(fft3d_handle plan, int cluster);
  * run).  dims: ngroups x 3 ints (n0, n1, n2) (host); counts: fields per group
  * (host).  Group i is a plan of batch counts[i]; fft3d_group_r2c / c2r take
  * host arrays of ngroups device pointers (group i's fields contiguous, layouts
- * as for fft3d_r2c / fft3d_c2r; c2r clobbers its inputs).  The groups run on
- * internal streams forked from and joined back into stream; on a non-default
- * stream the whole group is captured once per operand set into a CUDA graph
- * and replayed with a single graph launch.  fft3d_group_plan_at gives group i's
- * plan (for fft3d_autotune / fft3d_set_choices; tune before the first call
+ * as for fft3d_r2c / fft3d_c2r; c2r clobbers its inputs); fft3d_group_r2c_c2r
+ * runs the forward of in into mid and then the inverse of mid (clobbered)
+ * into out, as one call.  On a non-default stream each kind of call is
+ * captured once per operand set into a CUDA graph and replayed with a single
+ * graph launch.
+ *
+ * Two forms.  FFT3D_GROUP_STREAMS (the default): each size's plan runs its
+ * passes on an internal stream forked from and joined back into stream.
+ * FFT3D_GROUP_WORK_TABLE (offered wherever it applies: FP32, even n2, every n0
+ * and n1 in {64, 96, 128, 160, 192} and n2/2 in {32, 48, 64, 80, 96}): one
+ * persistent kernel launch per call runs every pass of every size (a work
+ * table of row / column tiles handed out in order; a tile of a size's pass
+ * waits, bounded, until that size's previous pass is complete); the round trip
+ * is one launch too.
+ * FFT3D_GROUP_WORK_TABLE_TEST_STALL is the work table with one dependency that
+ * cannot be met: its waits give up (about a second), set the timeout status
+ * and end the launch -- for testing fft3d_group_query_device_status only.
+ * fft3d_group_set_form returns FFT3D_ERR_INVALID_ARG for a form the group
+ * cannot run.  fft3d_group_plan_at gives group i's plan (for fft3d_autotune /
+ * fft3d_set_choices, which shape the streams form; tune before the first call
  * with a given operand set, since a captured graph keeps the launch shapes).
+ * fft3d_group_launches: kernel launches per call (dir -1 r2c, +1 c2r, 0 the
+ * round trip).  fft3d_group_query_device_status synchronises stream and
+ * returns FFT3D_ERR_TIMEOUT if a bounded wait of the group gave up.
  * dtype FFT3D_F64 is not offered (FFT3D_ERR_INVALID_ARG).
  */
+#define FFT3D_GROUP_STREAMS 0
+#define FFT3D_GROUP_WORK_TABLE 1
+#define FFT3D_GROUP_WORK_TABLE_TEST_STALL 2
 typedef struct fft3d_group_s* fft3d_group_handle;
 fft3d_group_handle fft3d_plan_group(const int* dims, const int* counts, int ngroups, int dtype);
 fft3d_handle fft3d_group_plan_at(fft3d_group_handle group, int i);
 int fft3d_group_r2c(fft3d_group_handle group, const float* const* in, void* const* out, void* stream);
 int fft3d_group_c2r(fft3d_group_handle group, void* const* in, float* const* out, void* stream);
+int fft3d_group_r2c_c2r(fft3d_group_handle group, const float* const* in, void* const* mid, float* const* out,
+                        void* stream);
 int fft3d_group_launches(fft3d_group_handle group, int dir);
+int fft3d_group_set_form(fft3d_group_handle group, int form);
+int fft3d_group_get_form(fft3d_group_handle group);
+int fft3d_group_query_device_status(fft3d_group_handle group, void* stream);
 void fft3d_group_destroy(fft3d_group_handle group);
 
 /*

@@ -28,6 +28,7 @@
 #include "energy.h"
 #include "fft3d.h"
 #include "cplane.h"
+#include "group_wt.h"
 #include "ns.h"
 #include "plane.h"
 #include "tma_host.h"
@@ -181,6 +182,10 @@ struct Axis {
     const LenEntry* spec = nullptr;
     const TcEntry* tc = nullptr;  // tensor-core radix-16 column kernel (TC dtypes)
     const SplitEntry* split[2] = {nullptr, nullptr};  // cluster-split column kernels of this length
+    const TmaSplitEntry* tsplit = nullptr;             // TMA-fed cluster split of this length
+    const L2SplitEntry* l2split = nullptr;             // residue split through L2 of this length (n0 axis)
+    float2* d_l2scratch = nullptr;                     // its scratch (plan-owned), for l2_ctas CTAs
+    int l2_ctas = 0;
     GenPlan gen{};
     float2* d_tw = nullptr;
     float2* d_blu = nullptr;  // Bluestein tables (chirp, bhat, W_M), lengths with a prime factor above 7
@@ -350,6 +355,65 @@ void find_split(int L, const SplitEntry* (&out)[2])
         if (e[i].L == L) out[k++] = &e[i];
 }
 
+const L2SplitEntry* find_l2split(int L)
+{
+    int n = 0;
+    const L2SplitEntry* e = l2split_entries(&n);
+    for (int i = 0; i < n; ++i)
+        if (e[i].L == L) return &e[i];
+    return nullptr;
+}
+
+const TmaSplitEntry* find_tma_split(int L)
+{
+    int n = 0;
+    const TmaSplitEntry* e = tma_split_entries(&n);
+    for (int i = 0; i < n; ++i)
+        if (e[i].L == L) return &e[i];
+    return nullptr;
+}
+
+// The TMA-fed cluster split runs a column pass when the residue views are
+// TMA-addressable: an even axis stride (16-byte aligned residue bases and row
+// strides), whole batch entries stacked at L * S, at least one tile of columns.
+bool tma_split_ok(const Axis& a, const ColArgs& ca)
+{
+    return a.tsplit && ca.S % 2 == 0 && ca.Bs == (long long)a.L * ca.S && ca.C >= 16 &&
+           ((uintptr_t)ca.data & 15) == 0;
+}
+
+cudaError_t run_l2split(const Axis& a, int dir, const ColArgs& ca, cudaStream_t s)
+{
+    SplitMaps maps{};
+    const int C = a.l2split->C;
+    for (int r = 0; r < C; ++r) {
+        const cudaError_t e = encode_tensor_map_2d(&maps.map[r], ca.data + r * ca.S, 2ull * ca.C,
+                                                   (unsigned long long)ca.nb * (a.L / C), 8ull * C * ca.S, 32, 256);
+        if (e != cudaSuccess) return e;
+    }
+    return dir < 0 ? a.l2split->fwd(ca, maps, a.d_l2scratch, a.l2_ctas, s)
+                   : a.l2split->inv(ca, maps, a.d_l2scratch, a.l2_ctas, s);
+}
+
+// The residue split through L2 applies to the n0 pass of the plan it was set up for.
+bool l2split_ok(const Axis& a, const ColArgs& ca)
+{
+    return a.l2split && a.d_l2scratch && ca.S % 2 == 0 && ca.Bs == (long long)a.L * ca.S && ca.C >= 16 &&
+           ((uintptr_t)ca.data & 15) == 0;
+}
+
+cudaError_t run_tma_split(const Axis& a, int dir, const ColArgs& ca, cudaStream_t s)
+{
+    SplitMaps maps{};
+    const int C = a.tsplit->C;
+    for (int r = 0; r < C; ++r) {
+        const cudaError_t e = encode_tensor_map_2d(&maps.map[r], ca.data + r * ca.S, 2ull * ca.C,
+                                                   (unsigned long long)ca.nb * (a.L / C), 8ull * C * ca.S, 32, 256);
+        if (e != cudaSuccess) return e;
+    }
+    return dir < 0 ? a.tsplit->fwd(ca, maps, s) : a.tsplit->inv(ca, maps, s);
+}
+
 const TcEntry* find_tc(int L)
 {
     int n = 0;
@@ -462,6 +526,7 @@ void free_plan(fft3d_plan_s* p)
         cudaFree(a->d_blu);
         cudaFree(a->d_tw64);
         cudaFree(a->d_blu64);
+        cudaFree(a->d_l2scratch);
     }
     cudaFree(p->d_twpack64);
     cudaFree(p->d_twpack);
@@ -555,7 +620,7 @@ bool tensor_map(fft3d_plan_s* p, const Axis& a, const ColArgs& ca, bool pair, CU
 const SplitEntry* split_choice(const fft3d_plan_s* p, const Axis& a)
 {
     const int form = (&a == &p->ax0) ? p->choice_tma : p->choice_tma1;
-    return form >= 2 ? a.split[form - 2] : nullptr;
+    return (form == 2 || form == 3) ? a.split[form - 2] : nullptr;
 }
 
 // One column pass with full control of the arguments (destination, mask, scale).
@@ -572,7 +637,9 @@ cudaError_t launch_col_args(fft3d_plan_s* p, const Axis& a, int dir, const ColAr
     if (uses_generic(p, a, false)) return generic_col(ca, a.gen, dir, s);
     const bool n0axis = (&a == &p->ax0);
     const int form = n0axis ? p->choice_tma : p->choice_tma1;
-    if (form >= 2 && a.split[form - 2]) {  // cluster-split kernel
+    if (form == 4 && tma_split_ok(a, ca)) return run_tma_split(a, dir, ca, s);  // TMA-fed cluster split
+    if (form == 5 && l2split_ok(a, ca)) return run_l2split(a, dir, ca, s);     // residue split through L2
+    if ((form == 2 || form == 3) && a.split[form - 2]) {  // cluster-split kernel
         const SplitEntry* se = a.split[form - 2];
         return dir < 0 ? se->fwd(ca, 0, s) : se->inv(ca, 0, s);
     }
@@ -635,6 +702,11 @@ std::string axis_desc(const fft3d_plan_s* p, const Axis& a, bool row)
                            : a.spec->row_rows;
         std::snprintf(b, sizeof b, "L=%d E=%d rows/CTA=%d %s", a.L, a.spec->row_E, rr,
                       a.spec->row_warp ? "warp" : "smem");
+    } else if (&a == &p->ax0 && p->choice_tma == 5 && a.l2split) {
+        std::snprintf(b, sizeof b, "L=%d E=32 cols/CTA=16 tma-residue-split C=%d via L2", a.L, a.l2split->C);
+    } else if (((&a == &p->ax0) ? p->choice_tma : p->choice_tma1) == 4 && a.tsplit &&
+               (&a == &p->ax0 ? p->P % 2 == 0 && p->P >= 16 : p->H % 2 == 0 && p->H >= 16)) {
+        std::snprintf(b, sizeof b, "L=%d E=32 cols/CTA=16 tma-cluster-split C=%d", a.L, a.tsplit->C);
     } else if (const SplitEntry* se = split_choice(p, a)) {
         std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d cluster-split C=%d", a.L, se->E, se->W, se->C);
     } else if (const int mode = (&a == &p->ax0) ? (p->choice_tma == 1 ? tma_mode(p, a, p->P, p->P, p->M) : 0)
@@ -834,7 +906,21 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
         // odd rows and the FP64 path: the runtime-length kernels
         a.spec = ((i == 2 && (n2 & 1)) || dtype == FFT3D_F64) ? nullptr : find_len(a.L);
         a.tc = (is_tc_dtype(dtype) && i < 2) ? find_tc(a.L) : nullptr;
-        if (a.spec && i < 2) find_split(a.L, a.split);
+        if (a.spec && i < 2) {
+            find_split(a.L, a.split);
+            a.tsplit = find_tma_split(a.L);
+        }
+        if (a.spec && i == 0 && p->P % 2 == 0 && p->P >= 16 && dtype == FFT3D_F32 &&
+            !(flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE)) {
+            // the residue split of the n0 pass and its scratch (one region per resident CTA)
+            if (const L2SplitEntry* le = find_l2split(a.L)) {
+                a.l2_ctas = le->ctas();
+                const size_t bytes = le->scratch_values(a.l2_ctas) * sizeof(float2);
+                if (a.l2_ctas > 0 && cudaMalloc((void**)&a.d_l2scratch, bytes) == cudaSuccess) a.l2split = le;
+                else a.l2_ctas = 0;
+                cudaGetLastError();  // a failed allocation only leaves the form out
+            }
+        }
         a.gen = generic_radices(a.L);
         if (upload(forward_table(a.L, a.L), &a.d_tw) != cudaSuccess ||
             (!smooth2357(a.L) && setup_bluestein(a) != cudaSuccess) ||
@@ -850,6 +936,10 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
     // and wherever its column tiles are wider than the TMA kernel's
     if (p->ax0.spec && p->ax0.spec->tma_W && (p->ax0.spec->col_W > p->ax0.spec->tma_W || p->ax0.L >= 1024))
         p->choice_tma = 0;
+    // n0 = 1024, 1536, 2048: the residue split through L2 where it applies
+    // (GB300, n0 pass: 1.94 vs 2.05 ms at 1024^3, 6.5-7.3 vs 8.4-8.5 ms at
+    // 1536 x 1024 x 2048, 18.9-19.6 vs 22.3-22.5 ms at 2048^3)
+    if (p->ax0.l2split) p->choice_tma = 5;
     if (is_tc_dtype(dtype)) {
         if (!p->ax0.tc && !p->ax1.tc) {  // no axis with a tensor-core kernel: the form does not exist here
             free_plan(p);
@@ -1473,7 +1563,10 @@ int fft3d_get_choices(fft3d_handle p, int* c)
 int fft3d_set_choices(fft3d_handle p, const int* c)
 {
     // column forms: 0 plain, 1 TMA ring, 2 + i the axis's i-th cluster-split kernel (must exist)
-    auto form_ok = [](int f, const Axis& a) { return f == 0 || f == 1 || ((f == 2 || f == 3) && a.split[f - 2]); };
+    auto form_ok = [](int f, const Axis& a) {
+        return f == 0 || f == 1 || ((f == 2 || f == 3) && a.split[f - 2]) || (f == 4 && a.tsplit) ||
+               (f == 5 && a.l2split);
+    };
     if (!p || !c || c[0] < 0 || c[1] < 0 || c[2] < 0 || !form_ok(c[3], p->ax0) || !form_ok(c[4], p->ax1))
         return fail(FFT3D_ERR_INVALID_ARG);
     p->choice_w0 = c[0];
@@ -1544,11 +1637,11 @@ int fft3d_autotune(fft3d_handle p, float* real, void* cplx, int reps, void* stre
             if (t < best) best = t, pick = w, pick_tma = 0;
         }
         p->choice_w1 = pick;
-        for (int i = 0; i < 2; ++i) {  // cluster-split kernels
-            if (!p->ax1.split[i]) continue;
-            p->choice_tma1 = 2 + i;
+        for (int f = 2; f <= 4; ++f) {  // cluster-split kernels, plain and TMA-fed
+            if (f < 4 ? !p->ax1.split[f - 2] : (!p->ax1.tsplit || H % 2 || H < 16)) continue;
+            p->choice_tma1 = f;
             const float t = time_pass([&] { run_col(p, p->ax1, -1, X, H, H, B * n0, n1 * H, s); }, reps, s);
-            if (t < best) best = t, pick_tma = 2 + i;
+            if (t < best) best = t, pick_tma = f;
         }
         p->choice_tma1 = pick_tma;
     }
@@ -1568,11 +1661,13 @@ int fft3d_autotune(fft3d_handle p, float* real, void* cplx, int reps, void* stre
             if (t < best) best = t, pick_w = w, pick_tma = 0;
         }
         p->choice_w0 = pick_w;
-        for (int i = 0; i < 2; ++i) {  // cluster-split kernels
-            if (!p->ax0.split[i]) continue;
-            p->choice_tma = 2 + i;
+        for (int f = 2; f <= 5; ++f) {  // split kernels: cluster (plain, TMA-fed), residues through L2
+            if (f < 4 ? !p->ax0.split[f - 2]
+                      : f == 4 ? (!p->ax0.tsplit || p->P % 2 || p->P < 16) : !p->ax0.l2split)
+                continue;
+            p->choice_tma = f;
             const float t = time_pass([&] { run_col(p, p->ax0, -1, X, p->P, p->P, B, p->M, s); }, reps, s);
-            if (t < best) best = t, pick_tma = 2 + i;
+            if (t < best) best = t, pick_tma = f;
         }
         p->choice_tma = pick_tma;
     }
@@ -1614,17 +1709,22 @@ struct fft3d_group_s {
     cudaEvent_t fork = nullptr;
     struct Graph {
         std::vector<const void*> in;
+        std::vector<void*> mid;
         std::vector<void*> out;
-        int dir = 0;
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
-    } graphs[2];  // one per direction
+    } graphs[3];  // forward, inverse, forward + inverse
+    // work-table form: every size has compiled item bodies
+    bool wt_ok = false;
+    int form = 0;                  // FFT3D_GROUP_STREAMS, FFT3D_GROUP_WORK_TABLE (or the test form)
+    WtCounters* d_ctr = nullptr;   // counters of one launch (zeroed before it)
 };
 
 namespace {
 
 void group_free(fft3d_group_s* g)
 {
+    cudaFree(g->d_ctr);
     for (auto& gr : g->graphs) {
         if (gr.exec) cudaGraphExecDestroy(gr.exec);
         if (gr.graph) cudaGraphDestroy(gr.graph);
@@ -1634,6 +1734,88 @@ void group_free(fft3d_group_s* g)
     for (auto e : g->joins) cudaEventDestroy(e);
     if (g->fork) cudaEventDestroy(g->fork);
     delete g;
+}
+
+// Segments of one pass of every size (largest first) into the work table.
+// pass: 0 rows, 1 n1, 2 n0; prev[i]: the segment size i's pass depends on
+// (-1: none); on return prev[i] is this pass's segment of size i.
+int wt_add_pass(const fft3d_group_s* g, WtTable& t, int pass, int dir, const void* const* rin, void* const* rout,
+                void* const* spec, std::vector<int>& prev)
+{
+    std::vector<size_t> order(g->plans.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        return g->plans[a]->batch * g->plans[a]->N > g->plans[b]->batch * g->plans[b]->N;
+    });
+    for (size_t i : order) {
+        const fft3d_plan_s* p = g->plans[i];
+        if (t.nseg >= kWtMaxSeg) return FFT3D_ERR_UNSUPPORTED_SIZE;
+        WtSeg& sg = t.seg[t.nseg];
+        sg = WtSeg{};
+        int per = 0;
+        const long long B = p->batch, n0 = p->n0, n1 = p->n1, H = p->H;
+        if (pass == 0) {
+            sg.body = wt_body_index(true, p->n2 / 2, dir, &per);
+            sg.rows = B * n0 * n1;
+            sg.items = (sg.rows + per - 1) / per;
+            sg.in = dir < 0 ? rin[i] : spec[i];
+            sg.out = dir < 0 ? spec[i] : rout[i];
+            sg.rs = p->n2 / 2;
+            sg.tw = p->ax2.d_tw;
+            sg.twpack = p->d_twpack;
+        } else {
+            const Axis& a = pass == 1 ? p->ax1 : p->ax0;
+            sg.body = wt_body_index(false, a.L, dir, &per);
+            sg.data = (float2*)spec[i];
+            sg.S = pass == 1 ? H : p->P;
+            sg.C = sg.S;
+            sg.nb = pass == 1 ? B * n0 : B;
+            sg.Bs = pass == 1 ? n1 * H : p->M;
+            sg.items = sg.nb * ((sg.C + per - 1) / per);
+            sg.tw = a.d_tw;
+        }
+        if (sg.body < 0) return FFT3D_ERR_UNSUPPORTED_SIZE;
+        sg.dep = prev[i];
+        sg.need = sg.dep >= 0 ? t.seg[sg.dep].items : 0;
+        sg.first = t.total;
+        t.total += sg.items;
+        prev[i] = t.nseg++;
+    }
+    return FFT3D_OK;
+}
+
+// The work table of a forward (dir < 0: in = real, mid = spectra), an inverse
+// (dir > 0: mid = spectra, out = real) or both (dir == 0), in the reverse pass
+// order for the inverse (Sec. 2.1).
+int wt_build(const fft3d_group_s* g, int dir, const void* const* rin, void* const* mid, void* const* rout,
+             WtTable& t)
+{
+    t.nseg = 0;
+    t.total = 0;
+    const int stall = g->form == FFT3D_GROUP_WORK_TABLE_TEST_STALL;
+    std::vector<int> prev(g->plans.size(), -1);
+    int st = FFT3D_OK;
+    if (dir <= 0)
+        for (int pass = 0; pass < 3 && st == FFT3D_OK; ++pass) st = wt_add_pass(g, t, pass, -1, rin, rout, mid, prev);
+    if (dir >= 0)
+        for (int pass = 2; pass >= 0 && st == FFT3D_OK; --pass) st = wt_add_pass(g, t, pass, +1, rin, rout, mid, prev);
+    if (stall)  // test form: the first dependency waits for one item more than exists
+        for (int i = 0; i < t.nseg; ++i)
+            if (t.seg[i].dep >= 0) {
+                t.seg[i].need += 1;
+                break;
+            }
+    return st;
+}
+
+int group_enqueue_wt(fft3d_group_s* g, int dir, const void* const* rin, void* const* mid, void* const* rout,
+                     cudaStream_t s)
+{
+    WtTable t;
+    const int st = wt_build(g, dir, rin, mid, rout, t);
+    if (st != FFT3D_OK) return st;
+    if (cudaMemsetAsync(g->d_ctr, 0, sizeof(WtCounters), s) != cudaSuccess) return FFT3D_ERR_CUDA;
+    return launch_wt(t, g->d_ctr, s) == cudaSuccess ? FFT3D_OK : FFT3D_ERR_CUDA;
 }
 
 int group_enqueue(fft3d_group_s* g, int dir, const void* const* in, void* const* out, cudaStream_t s)
@@ -1650,26 +1832,36 @@ int group_enqueue(fft3d_group_s* g, int dir, const void* const* in, void* const*
     return FFT3D_OK;
 }
 
-int group_exec(fft3d_group_s* g, int dir, const void* const* in, void* const* out, cudaStream_t s)
+// dir < 0: in -> mid (forward); dir > 0: mid -> out (inverse); dir == 0: both.
+int group_run(fft3d_group_s* g, int dir, const void* const* in, void* const* mid, void* const* out, cudaStream_t s)
+{
+    if (g->form != FFT3D_GROUP_STREAMS) return group_enqueue_wt(g, dir, in, mid, out, s);
+    int st = FFT3D_OK;
+    if (dir <= 0) st = group_enqueue(g, -1, in, mid, s);
+    if (st == FFT3D_OK && dir >= 0) st = group_enqueue(g, +1, const_cast<const void* const*>(mid), out, s);
+    return st;
+}
+
+int group_exec(fft3d_group_s* g, int dir, const void* const* in, void* const* mid, void* const* out, cudaStream_t s)
 {
     const size_t n = g->plans.size();
-    if (!in || !out) return fail(FFT3D_ERR_INVALID_ARG);
     for (size_t i = 0; i < n; ++i)
-        if (!in[i] || !out[i]) return fail(FFT3D_ERR_INVALID_ARG);
-    if (!s) {  // the legacy default stream cannot be captured: fork/join directly
-        const int st = group_enqueue(g, dir, in, out, s);
+        if ((dir <= 0 && !in[i]) || !mid[i] || (dir >= 0 && !out[i])) return fail(FFT3D_ERR_INVALID_ARG);
+    if (!s) {  // the legacy default stream cannot be captured: launch directly
+        const int st = group_run(g, dir, in, mid, out, s);
         return st == FFT3D_OK ? FFT3D_OK : fail(st);
     }
-    auto& gr = g->graphs[dir < 0 ? 0 : 1];
-    bool same = gr.exec != nullptr && gr.in.size() == n;
-    for (size_t i = 0; same && i < n; ++i) same = gr.in[i] == in[i] && gr.out[i] == out[i];
+    auto& gr = g->graphs[dir < 0 ? 0 : dir > 0 ? 1 : 2];
+    bool same = gr.exec != nullptr && gr.mid.size() == n;
+    for (size_t i = 0; same && i < n; ++i)
+        same = (dir > 0 || gr.in[i] == in[i]) && gr.mid[i] == mid[i] && (dir < 0 || gr.out[i] == out[i]);
     if (!same) {
         if (gr.exec) cudaGraphExecDestroy(gr.exec);
         if (gr.graph) cudaGraphDestroy(gr.graph);
         gr.exec = nullptr;
         gr.graph = nullptr;
         if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
-        const int st = group_enqueue(g, dir, in, out, s);
+        const int st = group_run(g, dir, in, mid, out, s);
         cudaGraph_t graph = nullptr;
         const cudaError_t e = cudaStreamEndCapture(s, &graph);
         if (st != FFT3D_OK || e != cudaSuccess || !graph) {
@@ -1682,8 +1874,9 @@ int group_exec(fft3d_group_s* g, int dir, const void* const* in, void* const* ou
             gr.graph = nullptr;
             return fail(FFT3D_ERR_CUDA);
         }
-        gr.in.assign(in, in + n);
-        gr.out.assign(out, out + n);
+        gr.in.assign(in ? in : mid, (in ? in : mid) + n);
+        gr.mid.assign(mid, mid + n);
+        gr.out.assign(out ? out : mid, (out ? out : mid) + n);
     }
     return cudaGraphLaunch(gr.exec, s) == cudaSuccess ? FFT3D_OK : fail(FFT3D_ERR_CUDA);
 }
@@ -1734,6 +1927,28 @@ fft3d_group_handle fft3d_plan_group(const int* dims, const int* counts, int ngro
         fail(FFT3D_ERR_CUDA);
         return nullptr;
     }
+    // the work-table form needs compiled item bodies for every size's passes
+    g->wt_ok = dtype == FFT3D_F32;
+    for (const fft3d_plan_s* p : g->plans) {
+        if (!g->wt_ok) break;
+        g->wt_ok = !(p->n2 & 1) && !(p->flags & FFT3D_FLAG_GENERIC) && p->ax0.spec && p->ax1.spec && p->ax2.spec;
+        for (int dir : {-1, 1})
+            g->wt_ok = g->wt_ok && wt_body_index(true, p->n2 / 2, dir, nullptr) >= 0 &&
+                       wt_body_index(false, p->n1, dir, nullptr) >= 0 && wt_body_index(false, p->n0, dir, nullptr) >= 0;
+    }
+    WtTable probe;  // the table fits (segment count) -- operands are not needed to know that
+    std::vector<void*> none(g->plans.size(), nullptr);
+    if (g->wt_ok && wt_build(g, 0, const_cast<const void* const*>(none.data()), none.data(), none.data(), probe) != FFT3D_OK)
+        g->wt_ok = false;
+    if (g->wt_ok && cudaMalloc((void**)&g->d_ctr, sizeof(WtCounters)) != cudaSuccess) {
+        group_free(g);
+        fail(FFT3D_ERR_ALLOC);
+        return nullptr;
+    }
+    // the streams form is the default: on GB300 it runs the 64^3 ... 192^3 x 4
+    // group in 685-741 us per r2c + c2r against 853 us for the work table (whose
+    // one register budget for every body holds it to 24 warps per SM)
+    g->form = FFT3D_GROUP_STREAMS;
     return g;
 }
 
@@ -1748,23 +1963,67 @@ fft3d_handle fft3d_group_plan_at(fft3d_group_handle g, int i)
 
 int fft3d_group_r2c(fft3d_group_handle g, const float* const* in, void* const* out, void* stream)
 {
-    if (!g) return fail(FFT3D_ERR_INVALID_ARG);
-    return group_exec(g, -1, reinterpret_cast<const void* const*>(in), out, (cudaStream_t)stream);
+    if (!g || !in || !out) return fail(FFT3D_ERR_INVALID_ARG);
+    return group_exec(g, -1, reinterpret_cast<const void* const*>(in), out, nullptr, (cudaStream_t)stream);
 }
 
 int fft3d_group_c2r(fft3d_group_handle g, void* const* in, float* const* out, void* stream)
 {
-    if (!g) return fail(FFT3D_ERR_INVALID_ARG);
-    return group_exec(g, +1, const_cast<const void* const*>(in), reinterpret_cast<void* const*>(out),
+    if (!g || !in || !out) return fail(FFT3D_ERR_INVALID_ARG);
+    return group_exec(g, +1, nullptr, in, reinterpret_cast<void* const*>(out), (cudaStream_t)stream);
+}
+
+int fft3d_group_r2c_c2r(fft3d_group_handle g, const float* const* in, void* const* mid, float* const* out,
+                        void* stream)
+{
+    if (!g || !in || !mid || !out) return fail(FFT3D_ERR_INVALID_ARG);
+    return group_exec(g, 0, reinterpret_cast<const void* const*>(in), mid, reinterpret_cast<void* const*>(out),
                       (cudaStream_t)stream);
 }
 
 int fft3d_group_launches(fft3d_group_handle g, int dir)
 {
     if (!g) return fail(FFT3D_ERR_INVALID_ARG);
+    if (g->form != FFT3D_GROUP_STREAMS) return 1;  // one work-table launch per call
     int n = 0;
-    for (auto* p : g->plans) n += fft3d_launches_per_call(p, dir);
+    for (auto* p : g->plans) n += (dir <= 0 ? fft3d_launches_per_call(p, -1) : 0) + (dir >= 0 ? fft3d_launches_per_call(p, 1) : 0);
     return n;
+}
+
+int fft3d_group_set_form(fft3d_group_handle g, int form)
+{
+    if (!g || (form != FFT3D_GROUP_STREAMS && form != FFT3D_GROUP_WORK_TABLE &&
+               form != FFT3D_GROUP_WORK_TABLE_TEST_STALL) ||
+        (form != FFT3D_GROUP_STREAMS && !g->wt_ok))
+        return fail(FFT3D_ERR_INVALID_ARG);
+    if (form != g->form)
+        for (auto& gr : g->graphs) {  // captured graphs hold the other form's launches
+            if (gr.exec) cudaGraphExecDestroy(gr.exec);
+            if (gr.graph) cudaGraphDestroy(gr.graph);
+            gr = fft3d_group_s::Graph{};
+        }
+    g->form = form;
+    return FFT3D_OK;
+}
+
+int fft3d_group_get_form(fft3d_group_handle g)
+{
+    if (!g) return -fail(FFT3D_ERR_INVALID_ARG);
+    return g->form;
+}
+
+int fft3d_group_query_device_status(fft3d_group_handle g, void* stream)
+{
+    if (!g) return fail(FFT3D_ERR_INVALID_ARG);
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
+    int st = 0;
+    if (g->d_ctr && cudaMemcpy(&st, &g->d_ctr->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(FFT3D_ERR_CUDA);
+    for (auto* p : g->plans) {
+        const int ps = fft3d_query_device_status(p, stream);
+        if (ps != FFT3D_OK) return ps;
+    }
+    return (st & kStatusTimeout) ? fail(FFT3D_ERR_TIMEOUT) : FFT3D_OK;
 }
 
 void fft3d_group_destroy(fft3d_group_handle g)

@@ -155,6 +155,30 @@ struct SplitEntry {
 };
 const SplitEntry* split_entries(int* n);
 
+// TMA-fed split (colsplit.cuh): L = 512 C, one tensor map per residue r of
+// the rows (base + r S, row stride C S).
+struct SplitMaps {
+    CUtensorMap map[4];
+};
+using ColTmaSplitFn = cudaError_t (*)(const ColArgs&, const SplitMaps&, cudaStream_t);
+struct TmaSplitEntry {
+    int L, C;
+    ColTmaSplitFn fwd, inv;
+};
+const TmaSplitEntry* tma_split_entries(int* n);
+
+// Residue split through L2 (colsplit.cuh): L = 512 C, one CTA per tile, the
+// residues parked in a scratch region of device memory (scratch_values(ctas)
+// float2 values for a grid of ctas CTAs).
+using ColL2SplitFn = cudaError_t (*)(const ColArgs&, const SplitMaps&, float2* scratch, int ctas, cudaStream_t);
+struct L2SplitEntry {
+    int L, C;
+    ColL2SplitFn fwd, inv;
+    size_t (*scratch_values)(int ctas);
+    int (*ctas)();  // grid size on the current device (resident CTAs)
+};
+const L2SplitEntry* l2split_entries(int* n);
+
 // Generic kernels: dir = -1 forward, +1 inverse.
 cudaError_t generic_col(const ColArgs& a, const GenPlan& g, int dir, cudaStream_t s);
 cudaError_t generic_row(const RowArgs& a, const GenPlan& g, int dir, cudaStream_t s);

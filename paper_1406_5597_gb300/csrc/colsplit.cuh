@@ -143,4 +143,407 @@ inline cudaError_t launch_col_split(const ColArgs& a, int /*w*/, cudaStream_t s)
     return cudaLaunchKernelEx(&cfg, k, a);
 }
 
+// ---------------------------------------------------------------------------
+// TMA-fed form of the split: every CTA of the cluster runs the 512-row
+// sub-transform of the persistent TMA column kernel (16-column tiles of
+// 128-byte rows, a two-slot ring kept full by one elected thread, bulk tensor
+// copies counted on mbarriers), L = 512 C.  The residue-r rows of a tile are
+// rows 512 b + a of a 2D view of the volume with base r*P (P = n1 (n2/2+1))
+// and row stride C*P, so each CTA reads its own tensor map.  Clusters are
+// persistent: cluster i takes tiles i, i + nclusters, ...
+//
+// Per tile: wait for the slot (bounded), agree across the cluster that every
+// CTA's copies arrived (each CTA writes its flag into every peer's shared
+// memory before the first cluster barrier; a failed wait on any CTA makes
+// the whole cluster stop after that barrier, so no CTA is left waiting at a
+// later one), refill the other slot, transform in registers with the slot as
+// exchange buffer, twiddle, push the peers' k' ranges (thread to thread),
+// second cluster barrier, radix-C step of the own k' range, stores straight
+// from registers.  The first barrier of the next tile also tells a CTA that
+// its peers have read the previous tile's pushes.  A wait that gives up sets
+// kStatusTimeout and the CTA drains its own copies (bounded) before it ends.
+// Requirements (checked by the host): P even (16-byte aligned residue
+// bases), Bs = L*P.
+// ---------------------------------------------------------------------------
+constexpr int kSplitLC = 512;  // rows per CTA
+constexpr int kSplitE = 32;    // values per thread
+constexpr int kSplitW = 16;    // columns per tile (128-byte rows)
+
+template <int C>
+struct TmaSplitGeom {
+    static constexpr int L = kSplitLC * C;
+    static constexpr int T = kSplitLC / kSplitE;  // 16 threads per column
+    static constexpr int NT = kSplitW * T;         // 256 threads
+    static constexpr int STAGES = 2;
+    static constexpr unsigned TILE_BYTES = (unsigned)kSplitLC * kSplitW * sizeof(float2);  // 64 KB
+    // k' split: CTA r takes registers m in [mlo(r), mlo(r+1))
+    __host__ __device__ static constexpr int mlo(int r) { return r * kSplitE / C; }
+    static constexpr int MAXEC = (kSplitE + C - 1) / C;
+    __host__ __device__ static constexpr int owner(int m)
+    {
+        int r = 0;
+        while (r + 1 < C && m >= mlo(r + 1)) ++r;
+        return r;
+    }
+    static constexpr size_t ring = (size_t)STAGES * TILE_BYTES;
+    static constexpr size_t rbytes = (size_t)(C - 1) * MAXEC * NT * sizeof(float2);
+    static constexpr size_t smem = ring + rbytes + 64 + 16 * C;  // + mbarriers + agreement flags
+};
+
+template <int C, int DIR>
+__global__ void __launch_bounds__(TmaSplitGeom<C>::NT) col_tma_split_kernel(const __grid_constant__ SplitMaps maps,
+                                                                           ColArgs a, long long ntiles)
+{
+    using G = TmaSplitGeom<C>;
+    constexpr int L = G::L, LC = kSplitLC, E = kSplitE, W = kSplitW, T = G::T, NT = G::NT, STAGES = G::STAGES;
+    constexpr int MAXEC = G::MAXEC;
+    constexpr int BOXR = 256, NBOX = LC / BOXR;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    float2* ring = reinterpret_cast<float2*>(smraw);
+    float2* rbuf = reinterpret_cast<float2*>(smraw + G::ring);
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smraw + G::ring + G::rbytes);
+    int* okf = reinterpret_cast<int*>(smraw + G::ring + G::rbytes + 64);
+    const int c = threadIdx.x, t = threadIdx.y;
+    const int tid = t * W + c;
+    const bool leader = (tid == 0);
+    const int rank = (int)cluster_ctarank();
+    const CUtensorMap* map = &maps.map[rank];
+    const long long ctiles = (a.C + W - 1) / W;
+    const long long cl = cluster_index(), ncl = cluster_count();
+    long long n_issued = 0;
+
+    if (leader) {
+        prefetch_tensormap(map);
+#pragma unroll
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    cluster_sync_all();  // every CTA of the cluster runs before the first remote store
+
+    auto issue = [&](long long tile, int s) {
+        if (tile >= ntiles) return;
+        const long long b = tile / ctiles;
+        const long long c0 = (tile - b * ctiles) * W;
+        mbar_arrive_expect_tx(&bars[s], G::TILE_BYTES);
+        float2* slot = ring + (size_t)s * LC * W;
+#pragma unroll
+        for (int k = 0; k < NBOX; ++k)
+            tma_load_2d(slot + (size_t)k * BOXR * W, map, (int)(2 * c0), (int)(b * LC + k * BOXR), &bars[s]);
+        ++n_issued;
+    };
+
+    if (leader) issue(cl, 0);
+    TwCache<LC, E, C> twc;  // the sub-transform's twiddles (table of length L: every C-th entry)
+    twc.fill(a.tw, t);
+    int stage = 0;
+    unsigned phase = 0;
+    long long n_consumed = 0;
+    bool failed = false;
+    for (long long tile = cl; tile < ntiles; tile += ncl) {
+        const bool ok = __syncthreads_and(mbar_wait_bounded(&bars[stage], phase, kMbarMaxTries));
+        // cluster-wide agreement that every CTA has its tile
+        if (leader) {
+#pragma unroll
+            for (int p = 0; p < C; ++p) {
+                if (p == rank) okf[rank] = ok;
+                else asm volatile("st.shared::cluster.u32 [%0], %1;\n" ::"r"(dsmem_map(&okf[rank], (unsigned)p)),
+                                  "r"((unsigned)ok)
+                                  : "memory");
+            }
+        }
+        cluster_arrive_release();
+        cluster_wait_acquire();
+        bool all_ok = true;
+#pragma unroll
+        for (int p = 0; p < C; ++p) all_ok = all_ok && (okf[p] != 0);
+        if (!all_ok) {
+            failed = true;
+            if (ok) ++n_consumed;
+            break;
+        }
+        ++n_consumed;
+        if (leader) issue(tile + ncl, stage ^ 1);  // the other slot was consumed in the previous iteration
+        const long long b = tile / ctiles;
+        const long long c0 = (tile - b * ctiles) * W;
+        const bool active = (c0 + c) < a.C;
+        float2* buf = ring + (size_t)stage * LC * W;
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = buf[(t + T * m) * W + c];
+        __syncthreads();  // the slot now serves as the exchange buffer
+        fft_group<LC, E, DIR, C>(v, t, twc, ColExchange{buf, W, c});
+        fence_proxy_async_smem();  // order this thread's shared accesses before the slot's next bulk copy
+        if (rank > 0) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = twiddle<DIR>(v[m], __ldg(&a.tw[rank * (t + T * m)]));
+        }
+        // push registers m to their owner CTA (its slot for this CTA)
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int r = G::owner(m);
+            if (r != rank) {
+                const int slot = rank - (rank > r ? 1 : 0);
+                dsmem_st(dsmem_map(&rbuf[(slot * MAXEC + (m - G::mlo(r))) * NT + tid], (unsigned)r), v[m]);
+            }
+        }
+        cluster_arrive_release();
+        cluster_wait_acquire();  // every peer's pushes are visible
+        float2* dst = (a.dst ? a.dst : a.data) + b * a.Bs + c0 + c;
+#pragma unroll
+        for (int r = 0; r < C; ++r) {
+            if (r != rank) continue;
+#pragma unroll
+            for (int m = G::mlo(r); m < G::mlo(r + 1); ++m) {
+                float2 z[C];
+#pragma unroll
+                for (int s = 0; s < C; ++s)
+                    z[s] = (s == r) ? v[m] : rbuf[((s - (s > r ? 1 : 0)) * MAXEC + (m - G::mlo(r))) * NT + tid];
+                Dft<C, DIR>::run(z);
+                const int kp = t + T * m;
+                if (active) {
+                    if (a.mask23 == 0 && a.scale == 1.0f) {
+#pragma unroll
+                        for (int s = 0; s < C; ++s) dst[(long long)(kp + LC * s) * a.S] = z[s];
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < C; ++s)
+                            dst[(long long)(kp + LC * s) * a.S] =
+                                cscale(z[s], col_out_factor(kp + LC * s, L, a.scale, a.mask23));
+                    }
+                }
+            }
+        }
+        stage ^= 1;
+        if (stage == 0) phase ^= 1u;
+    }
+    if (failed && leader) {
+        atomicOr(a.status, kStatusTimeout);
+        // drain: wait (bounded) for every copy issued but not consumed
+        for (long long k = n_consumed; k < n_issued; ++k)
+            mbar_wait_bounded(&bars[k % STAGES], (unsigned)((k / STAGES) & 1), kMbarMaxTries);
+    }
+}
+
+// Persistent clusters of C CTAs, as many as are co-resident; one tensor map
+// per residue.  Requirements: P = a.S / C even, a.Bs = L * a.S / C.
+template <int C, int DIR>
+inline cudaError_t launch_col_tma_split(const ColArgs& a, const SplitMaps& maps, cudaStream_t s)
+{
+    using G = TmaSplitGeom<C>;
+    auto k = col_tma_split_kernel<C, DIR>;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kSplitW, G::T);
+    cfg.dynamicSmemBytes = G::smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    static PerDevice resident;  // co-resident clusters, queried once per device
+    int max_clusters = 0;
+    cudaError_t e = per_device(resident, &max_clusters, [&](int, int* v) {
+        cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
+        if (r != cudaSuccess) return r;
+        cfg.gridDim = dim3(C * 64);
+        return cudaOccupancyMaxActiveClusters(v, k, &cfg);
+    });
+    if (e != cudaSuccess) return e;
+    const long long ntiles = a.nb * ((a.C + kSplitW - 1) / kSplitW);
+    if (ntiles <= 0) return cudaSuccess;
+    const long long ncl = ntiles < max_clusters ? ntiles : max_clusters;
+    cfg.gridDim = dim3((unsigned)(ncl * C));
+    return cudaLaunchKernelEx(&cfg, k, maps, a, ntiles);
+}
+
+// ---------------------------------------------------------------------------
+// Residue split through L2 (one CTA per tile, no cluster): a persistent CTA
+// takes the W = 16 columns x L rows of a tile (L = 512 C) as C residue
+// sub-tiles of 512 rows (rows C a + r), each fed by bulk tensor copies through
+// the two-slot ring of the TMA column kernel, one sub-tile ahead, so the next
+// tile's first sub-tile arrives while the current tile is combined.  For
+// residue r < C-1 the CTA runs the 512-point transform, twiddles by W^{r k'}
+// and parks the values in the CTA's own scratch region (device memory that
+// stays in L2: up to C-1 sub-tiles per CTA, up to 30 MB per GPU), or, with
+// PARK, residue C-2 in shared memory next to the ring (measured: faster at
+// C = 3, slower at C = 2 and 4, where the larger shared-memory carve-out
+// costs more than the L2 round trip saves); after the last residue
+// it reads them back (ld.global.cg: L2, never a stale L1 line; the loads of 8
+// outputs at a time issued together) and forms the radix-C outputs
+// X[k' + 512 s] from the last residue, written back into its slot.  Thread
+// (c, t) reads only the values it parked itself, so no barrier orders them.
+// DRAM sees one read and one write of the tile; the scratch traffic
+// (2 (C-2) sub-tiles per tile) stays in L2.  Every mbarrier wait is
+// bounded (a wait that gives up sets kStatusTimeout; the CTA drains its own
+// copies, bounded, and ends).
+// Requirements (checked by the host): P even, Bs = L*P, at least 16 columns.
+// ---------------------------------------------------------------------------
+template <int C, bool PARK>
+struct L2SplitGeom {
+    static constexpr int L = kSplitLC * C;
+    static constexpr int T = kSplitLC / kSplitE;  // 16 threads per column
+    static constexpr int NT = kSplitW * T;         // 256 threads
+    static constexpr int STAGES = 2;
+    static constexpr unsigned SUB_BYTES = (unsigned)kSplitLC * kSplitW * sizeof(float2);  // 64 KB
+    // PARK: residue C-2 is parked in shared memory next to the ring, the
+    // others (0 .. C-3, or 0 .. C-2 without PARK) in L2 scratch
+    static constexpr int NL2 = PARK ? C - 2 : C - 1;  // residues parked in L2
+    static constexpr size_t smem = (size_t)(STAGES + (PARK ? 1 : 0)) * SUB_BYTES + 64;
+    static constexpr size_t scratch_per_cta = (size_t)(NL2 > 0 ? NL2 : 1) * kSplitLC * kSplitW;  // float2 values
+};
+
+template <int C, int DIR, bool PARK>
+__global__ void __launch_bounds__(L2SplitGeom<C, PARK>::NT) col_l2split_kernel(const __grid_constant__ SplitMaps maps,
+                                                                              ColArgs a, float2* scratch,
+                                                                              long long ntiles)
+{
+    using G = L2SplitGeom<C, PARK>;
+    constexpr int NL2 = G::NL2;
+    constexpr int L = G::L, LC = kSplitLC, E = kSplitE, W = kSplitW, T = G::T, STAGES = G::STAGES;
+    constexpr int BOXR = 256, NBOX = LC / BOXR;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    float2* ring = reinterpret_cast<float2*>(smraw);
+    float2* park = ring + (size_t)STAGES * LC * W;  // PARK: residue C-2 (each thread's own positions)
+    unsigned long long* bars =
+        reinterpret_cast<unsigned long long*>(smraw + (size_t)(STAGES + (PARK ? 1 : 0)) * G::SUB_BYTES);
+    const int c = threadIdx.x, t = threadIdx.y;
+    const bool leader = (c == 0 && t == 0);
+    const long long ctiles = (a.C + W - 1) / W;
+    float2* mine = scratch + (size_t)blockIdx.x * G::scratch_per_cta + (size_t)t * W + c;  // + (r LC + T m) W
+    long long n_issued = 0;
+
+    if (leader) {
+#pragma unroll
+        for (int r = 0; r < C; ++r) prefetch_tensormap(&maps.map[r]);
+#pragma unroll
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // the CTA's n-th sub-tile: tile blockIdx.x + (n / C) gridDim.x, residue n % C
+    auto issue = [&](long long n) {
+        const long long tile = blockIdx.x + (n / C) * (long long)gridDim.x;
+        if (tile >= ntiles) return;
+        const int r = (int)(n % C), s = (int)(n & 1);
+        const long long b = tile / ctiles;
+        const long long c0 = (tile - b * ctiles) * W;
+        mbar_arrive_expect_tx(&bars[s], G::SUB_BYTES);
+        float2* slot = ring + (size_t)s * LC * W;
+#pragma unroll
+        for (int k = 0; k < NBOX; ++k)
+            tma_load_2d(slot + (size_t)k * BOXR * W, &maps.map[r], (int)(2 * c0), (int)(b * LC + k * BOXR), &bars[s]);
+        ++n_issued;
+    };
+
+    if (leader) issue(0);
+    long long n_consumed = 0;
+    bool failed = false;
+    for (long long n = 0;; ++n) {
+        const long long tile = blockIdx.x + (n / C) * (long long)gridDim.x;
+        if (tile >= ntiles) break;
+        const int r = (int)(n % C), s = (int)(n & 1);
+        const bool ok = mbar_wait_bounded(&bars[s], (unsigned)((n >> 1) & 1), kMbarMaxTries);
+        if (!__syncthreads_and(ok)) {
+            failed = true;
+            break;
+        }
+        ++n_consumed;
+        if (leader) issue(n + 1);  // into the slot consumed at n - 1
+        const long long b = tile / ctiles;
+        const long long c0 = (tile - b * ctiles) * W;
+        const bool active = (c0 + c) < a.C;
+        float2* buf = ring + (size_t)s * LC * W;
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = buf[(t + T * m) * W + c];
+        __syncthreads();  // the slot now serves as the exchange buffer
+        // (twiddles from the table: registers go to the combine's loads below)
+        fft_group<LC, E, DIR, C>(v, t, a.tw, ColExchange{buf, W, c});
+        if (r > 0) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = twiddle<DIR>(v[m], __ldg(&a.tw[r * (t + T * m)]));
+        }
+        if (PARK && r == C - 2) {  // parked in shared memory
+#pragma unroll
+            for (int m = 0; m < E; ++m) park[(t + T * m) * W + c] = v[m];
+            fence_proxy_async_smem();  // order this thread's shared accesses before the slot's next bulk copy
+            continue;
+        }
+        if (r < NL2) {  // parked in L2
+#pragma unroll
+            for (int m = 0; m < E; ++m) __stcg(&mine[((size_t)r * LC + T * m) * W], v[m]);
+            fence_proxy_async_smem();
+            continue;
+        }
+        // last residue: its values go back into the slot (each thread to the
+        // positions it alone reads), then the radix-C step with the parked
+        // residues, their L2 loads issued MB registers at a time so that they
+        // are in flight together
+#pragma unroll
+        for (int m = 0; m < E; ++m) buf[(t + T * m) * W + c] = v[m];
+        float2* dst = (a.dst ? a.dst : a.data) + b * a.Bs + c0 + c;
+        constexpr int MB = 8;
+#pragma unroll
+        for (int m0 = 0; m0 < E; m0 += MB) {
+            float2 z[MB][C];
+#pragma unroll
+            for (int mm = 0; mm < MB; ++mm)
+#pragma unroll
+                for (int q = 0; q < NL2; ++q) z[mm][q] = __ldcg(&mine[((size_t)q * LC + T * (m0 + mm)) * W]);
+#pragma unroll
+            for (int mm = 0; mm < MB; ++mm) {
+                if constexpr (PARK) z[mm][C - 2] = park[(t + T * (m0 + mm)) * W + c];
+                z[mm][C - 1] = buf[(t + T * (m0 + mm)) * W + c];
+                Dft<C, DIR>::run(z[mm]);
+                const int kp = t + T * (m0 + mm);
+                if (active) {
+                    if (a.mask23 == 0 && a.scale == 1.0f) {
+#pragma unroll
+                        for (int q = 0; q < C; ++q) dst[(long long)(kp + LC * q) * a.S] = z[mm][q];
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < C; ++q)
+                            dst[(long long)(kp + LC * q) * a.S] =
+                                cscale(z[mm][q], col_out_factor(kp + LC * q, L, a.scale, a.mask23));
+                    }
+                }
+            }
+        }
+        fence_proxy_async_smem();  // order this thread's shared accesses before the slot's next bulk copy
+    }
+    if (failed && leader) {
+        atomicOr(a.status, kStatusTimeout);
+        for (long long k = n_consumed; k < n_issued; ++k)
+            mbar_wait_bounded(&bars[k & 1], (unsigned)((k >> 1) & 1), kMbarMaxTries);
+    }
+}
+
+// Persistent: one CTA per resident slot (one per SM).  scratch: at least
+// l2split_scratch_values<C>(ctas) float2 values of device memory, ctas = the
+// grid size this launcher uses (l2split_ctas).
+template <int C, bool PARK>
+inline size_t l2split_scratch_values(int ctas)
+{
+    return (size_t)ctas * L2SplitGeom<C, PARK>::scratch_per_cta;
+}
+
+template <int C, int DIR, bool PARK>
+inline cudaError_t launch_col_l2split(const ColArgs& a, const SplitMaps& maps, float2* scratch, int ctas,
+                                      cudaStream_t s)
+{
+    using G = L2SplitGeom<C, PARK>;
+    auto k = col_l2split_kernel<C, DIR, PARK>;
+    static PerDevice limit;  // the shared memory limit, raised once per device
+    cudaError_t e = smem_limit_per_device(limit, k, G::smem);
+    if (e != cudaSuccess) return e;
+    const long long ntiles = a.nb * ((a.C + kSplitW - 1) / kSplitW);
+    if (ntiles <= 0) return cudaSuccess;
+    const long long grid = ntiles < ctas ? ntiles : ctas;
+    k<<<(unsigned)grid, dim3(kSplitW, G::T), G::smem, s>>>(maps, a, scratch, ntiles);
+    return cudaGetLastError();
+}
+
 }  // namespace fft3d

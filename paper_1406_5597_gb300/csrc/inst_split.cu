@@ -20,4 +20,41 @@ const SplitEntry* split_entries(int* n)
     return e;
 }
 
+const TmaSplitEntry* tma_split_entries(int* n)
+{
+    static const TmaSplitEntry e[] = {
+        {1024, 2, &fft3d::launch_col_tma_split<2, -1>, &fft3d::launch_col_tma_split<2, 1>},
+        {1536, 3, &fft3d::launch_col_tma_split<3, -1>, &fft3d::launch_col_tma_split<3, 1>},
+        {2048, 4, &fft3d::launch_col_tma_split<4, -1>, &fft3d::launch_col_tma_split<4, 1>},
+    };
+    *n = (int)(sizeof(e) / sizeof(e[0]));
+    return e;
+}
+
+template <int C, bool PARK>
+int l2split_ctas()
+{
+    static PerDevice resident;
+    int ctas = 0;
+    return resident_ctas_per_device(resident, col_l2split_kernel<C, -1, PARK>, L2SplitGeom<C, PARK>::NT,
+                                    L2SplitGeom<C, PARK>::smem, &ctas) == cudaSuccess
+               ? ctas
+               : 0;
+}
+
+#define FFT3D_L2SPLIT(L, C, PARK)                                                                       \
+    { L, C, &launch_col_l2split<C, -1, PARK>, &launch_col_l2split<C, 1, PARK>,                          \
+      &l2split_scratch_values<C, PARK>, &l2split_ctas<C, PARK> }
+
+const L2SplitEntry* l2split_entries(int* n)
+{
+    static const L2SplitEntry e[] = {
+        FFT3D_L2SPLIT(1024, 2, false),  // the other residue in L2
+        FFT3D_L2SPLIT(1536, 3, true),   // residue 1 in shared memory, residue 0 in L2
+        FFT3D_L2SPLIT(2048, 4, false),  // residues 0 .. 2 in L2
+    };
+    *n = (int)(sizeof(e) / sizeof(e[0]));
+    return e;
+}
+
 }  // namespace fft3d

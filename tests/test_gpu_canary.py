@@ -96,11 +96,19 @@ CASES = [
     ((1024, 3, 10), 1, "f32", "split1"),
     ((1536, 4, 12), 1, "f32", "split0"),
     ((2, 2048, 32), 1, "f32", "split0_n1"),     # the n1 pass, odd H
+    ((2048, 3, 10), 2, "f32", "tsplit"),        # TMA-fed cluster split, 4 CTAs, ragged tile, batch
+    ((1536, 2, 30), 1, "f32", "tsplit"),        # 3 CTAs
+    ((1024, 4, 12), 1, "f32", "tsplit"),        # 2 CTAs
+    ((2, 2048, 30), 1, "f32", "tsplit_n1"),     # the n1 pass (even H)
+    ((2048, 3, 10), 2, "f32", "l2split"),       # residue split through L2 scratch, C = 4, ragged, batch
+    ((1536, 2, 30), 1, "f32", "l2split"),       # C = 3
+    ((1024, 4, 12), 1, "f32", "l2split"),       # C = 2
 ]
 
 
 # column-form choices {w0, w1, rows, form0, form1} of the split cases
-SPLIT_CHOICES = {"split0": [0, 0, 0, 2, 0], "split1": [0, 0, 0, 3, 0], "split0_n1": [0, 0, 0, 0, 2]}
+SPLIT_CHOICES = {"split0": [0, 0, 0, 2, 0], "split1": [0, 0, 0, 3, 0], "split0_n1": [0, 0, 0, 0, 2],
+                 "tsplit": [0, 0, 0, 4, 0], "tsplit_n1": [0, 0, 0, 0, 4], "l2split": [0, 0, 0, 5, 0]}
 
 
 def _flags(lib, name):
@@ -126,7 +134,7 @@ def test_no_write_outside_the_operands(cuda_lib, shape, batch, dt, fl):
     plan = lib.Plan(n0, n1, n2, dtype=dtype, batch=batch, flags=flags)
     if fl in SPLIT_CHOICES:
         assert lib.fft3d_set_choices(plan.handle, SPLIT_CHOICES[fl]) == lib.FFT3D_OK
-        assert "cluster-split" in plan.describe()
+        assert "split" in plan.describe()
     rt = torch.float64 if f64 else torch.float32
     ct = torch.complex128 if f64 else torch.complex64
     row = 2 * H if fl == "padded" else n2

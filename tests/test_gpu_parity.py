@@ -665,37 +665,90 @@ def test_tensor_core_form_batched_and_unsupported(cuda_lib):
 GROUP_DIMS = [(64, 64, 64), (96, 96, 96), (128, 128, 128), (192, 192, 192), (160, 160, 160)]
 
 
-def test_grouped_uneven_batch_matches_oracle(cuda_lib):
+@pytest.mark.parametrize("form", ["work_table", "streams"])
+def test_grouped_uneven_batch_matches_oracle(cuda_lib, form):
+    """Both group forms (the persistent work-table launch, and the per-size
+    plans on forked streams): forward, inverse and the one-call round trip,
+    captured and replayed, and on the legacy default stream; every field of
+    every size against the oracle."""
     lib = cuda_lib
     counts = [4] * len(GROUP_DIMS)
     g = lib.Group(GROUP_DIMS, counts)
-    xs, Xs, refs = [], [], []
+    assert g.form == lib.FFT3D_GROUP_STREAMS  # the default
+    g.form = lib.FFT3D_GROUP_WORK_TABLE if form == "work_table" else lib.FFT3D_GROUP_STREAMS
+    xs, Xs, refs, Xrefs = [], [], [], []
     for i, (n0, n1, n2) in enumerate(GROUP_DIMS):
         x32 = synth.uniform_field((4, n0, n1, n2), seed=synth.seed_for_config(4, field=i + 1)).astype(np.float32)
         xs.append(torch.from_numpy(x32).cuda())
         Xs.append(torch.empty((4, n0, n1, n2 // 2 + 1), dtype=torch.complex64, device="cuda"))
         refs.append(x32)
+        Xrefs.append(oracle.r2c3d(x32.astype(np.float64)))
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
         g.r2c(xs, Xs, stream=s.cuda_stream)   # captured into one graph
         g.r2c(xs, Xs, stream=s.cuda_stream)   # replayed
     s.synchronize()
-    for i, (n0, n1, n2) in enumerate(GROUP_DIMS):
+    assert lib.fft3d_group_query_device_status(g.handle, 0) == lib.FFT3D_OK
+    for i in range(len(GROUP_DIMS)):
         got = Xs[i].cpu().numpy().astype(np.complex128)
-        for f in (0, 3):
-            assert rel_l2(got[f], oracle.r2c3d(refs[i][f].astype(np.float64))) <= TOL
-    # inverse on the legacy default stream (direct fork/join), inputs clobbered
+        for f in range(4):
+            assert rel_l2(got[f], Xrefs[i][f]) <= TOL, (i, f)
+    # inverse on the legacy default stream (launched directly), inputs clobbered
     Ys = [X.clone() for X in Xs]
     outs = [torch.empty_like(x) for x in xs]
     g.c2r(Ys, outs, stream=0)
     torch.cuda.synchronize()
     for i, (n0, n1, n2) in enumerate(GROUP_DIMS):
-        N = n0 * n1 * n2
         y = outs[i].cpu().numpy().astype(np.float64)
-        for f in (1, 2):
-            assert rel_l2(y[f] / N, refs[i][f].astype(np.float64)) <= TOL_RT
-    assert lib.fft3d_group_launches(g.handle, -1) == 15
+        ref = oracle.c2r3d(Xs[i].cpu().numpy().astype(np.complex128), n2)
+        for f in range(4):
+            assert rel_l2(y[f], ref[f]) <= TOL, (i, f)
+    # the round trip in one call (captured, replayed twice)
+    mids = [torch.empty_like(X) for X in Xs]
+    outs2 = [torch.full_like(x, float("nan")) for x in xs]
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            g.r2c_c2r(xs, mids, outs2, stream=s.cuda_stream)
+    s.synchronize()
+    for i, (n0, n1, n2) in enumerate(GROUP_DIMS):
+        N = n0 * n1 * n2
+        y = outs2[i].cpu().numpy().astype(np.float64)
+        for f in range(4):
+            assert rel_l2(y[f] / N, refs[i][f].astype(np.float64)) <= TOL_RT, (i, f)
+    if form == "work_table":
+        assert [lib.fft3d_group_launches(g.handle, d) for d in (-1, 1, 0)] == [1, 1, 1]
+    else:
+        assert lib.fft3d_group_launches(g.handle, -1) == 15 and lib.fft3d_group_launches(g.handle, 0) == 30
+    g.close()
+
+
+def test_group_work_table_availability_and_bounded_wait(cuda_lib):
+    """A group with a size that has no work-table bodies keeps the streams
+    form and refuses the work table; the test form with an unmeetable
+    dependency gives up (bounded), reports FFT3D_ERR_TIMEOUT, and the same
+    group then transforms correctly."""
+    lib = cuda_lib
+    g = lib.Group([(64, 64, 64), (250, 10, 12)], [1, 1])
+    assert g.form == lib.FFT3D_GROUP_STREAMS
+    assert lib.fft3d_group_set_form(g.handle, lib.FFT3D_GROUP_WORK_TABLE) == lib.FFT3D_ERR_INVALID_ARG
+    g.close()
+    dims = [(64, 64, 64), (96, 96, 96)]
+    g = lib.Group(dims, [1, 2])
+    xs = [torch.from_numpy(synth.uniform_field((c, *d), seed=70 + c).astype(np.float32)).cuda()
+          for d, c in zip(dims, (1, 2))]
+    Xs = [torch.empty((c, d[0], d[1], d[2] // 2 + 1), dtype=torch.complex64, device="cuda")
+          for d, c in zip(dims, (1, 2))]
+    g.form = lib.FFT3D_GROUP_WORK_TABLE_TEST_STALL
+    g.r2c(xs, Xs, stream=0)
+    assert lib.fft3d_group_query_device_status(g.handle, 0) == lib.FFT3D_ERR_TIMEOUT
+    g.form = lib.FFT3D_GROUP_WORK_TABLE
+    g.r2c(xs, Xs, stream=0)
+    torch.cuda.synchronize()
+    assert lib.fft3d_group_query_device_status(g.handle, 0) == lib.FFT3D_OK
+    for x, X in zip(xs, Xs):
+        ref = oracle.r2c3d(x.cpu().numpy().astype(np.float64))
+        assert rel_l2(X.cpu().numpy().astype(np.complex128), ref) <= TOL
     g.close()
 
 
@@ -752,14 +805,18 @@ def test_long_axis_column_forms_match_oracle(cuda_lib, shape):
 
 @pytest.mark.parametrize("shape,batch", [((2048, 2, 6), 1), ((1024, 3, 10), 1), ((1536, 4, 12), 1),
                                          ((2, 2048, 32), 1), ((3, 1024, 30), 1), ((1024, 2, 8), 2),
-                                         ((2048, 3, 4), 2)],
+                                         ((2048, 3, 4), 2), ((2048, 3, 10), 1), ((1024, 4, 12), 2),
+                                         ((1536, 2, 30), 1), ((2, 2048, 30), 1)],
                          ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else f"b{v}")
 def test_cluster_split_column_forms_match_oracle(cuda_lib, shape, batch):
     """The cluster-split column kernels (forms 2 and 3 of the n0 and n1
     passes: the tile's rows split by residue over a 2- or 4-CTA cluster, the
-    final radix-C step through distributed shared memory) give the oracle's
-    transform in both directions: ragged column tiles, batches, the n1 axis,
-    and the input-preserving inverse (its first pass writes elsewhere)."""
+    final radix-C step through distributed shared memory; form 4: the same
+    split with 512-row TMA-fed sub-transforms on 2, 3 or 4 CTAs; form 5: the
+    512-row residues of one CTA's tile, parked in L2 scratch) give the
+    oracle's transform in both directions: ragged column tiles, batches, the
+    n1 axis, and the input-preserving inverse (its first pass writes
+    elsewhere)."""
     lib = cuda_lib
     n0, n1, n2 = shape
     H = n2 // 2 + 1
@@ -772,14 +829,15 @@ def test_cluster_split_column_forms_match_oracle(cuda_lib, shape, batch):
     tried = 0
     for flags in (0, lib.FFT3D_FLAG_PRESERVE_INPUT):
         plan = lib.Plan(n0, n1, n2, lib.FFT3D_F32, batch, flags)
-        for f0 in (0, 2, 3):
-            for f1 in (0, 2, 3):
+        for f0 in (0, 2, 3, 4, 5):
+            for f1 in (0, 2, 3, 4):
                 if f0 < 2 and f1 < 2:
                     continue
                 if lib.fft3d_set_choices(plan.handle, [0, 0, 0, f0, f1]) != lib.FFT3D_OK:
                     continue  # no such form on this axis
+                if "split" not in plan.describe():
+                    continue  # form 4 on an axis whose stride it cannot take: the plain kernel runs
                 tried += 1
-                assert "cluster-split" in plan.describe()
                 X = torch.empty(lead + (n0, n1, H), dtype=torch.complex64, device="cuda")
                 plan.r2c(xd.data_ptr(), X.data_ptr())
                 torch.cuda.synchronize()
