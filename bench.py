@@ -722,7 +722,9 @@ def pseudo_spectral(ctx):
                                 "graph": True, "scheme": "Heun RK2, nu = 0.01, dt = 1e-3"}
     ns.close()
     del ns, U
-    # grouped uneven batch: 64^3, 96^3, 128^3, 192^3, 160^3 x 4 fields, r2c + c2r, shapes autotuned
+    # grouped uneven batch: 64^3, 96^3, 128^3, 192^3, 160^3 x 4 fields, r2c + c2r
+    # as one round-trip call (one graph): the work-table form (one persistent
+    # launch) and the per-size streams form (the default)
     gdims = [(64, 64, 64), (96, 96, 96), (128, 128, 128), (192, 192, 192), (160, 160, 160)]
     grp = fft3d.Group(gdims, [4] * len(gdims))
     gin, gmid, gout = [], [], []
@@ -730,23 +732,37 @@ def pseudo_spectral(ctx):
         gin.append(torch.randn((4, a0, a1, a2), device=dev))
         gmid.append(torch.empty((4, a0, a1, a2 // 2 + 1), dtype=torch.complex64, device=dev))
         gout.append(torch.empty((4, a0, a1, a2), device=dev))
-    for i in range(len(gdims)):
-        fft3d.fft3d_autotune(fft3d.fft3d_group_plan_at(grp.handle, i), gin[i].data_ptr(), gmid[i].data_ptr(), 3, sptr)
+    gbytes = sum(2 * 4 * (4 * a0 * a1 * a2 + 40 * a0 * a1 * (a2 // 2 + 1)) for (a0, a1, a2) in gdims)
     gs = torch.cuda.Stream(dev)
     gs.wait_stream(stream)
-    with torch.cuda.stream(gs):
-        def gstep():
-            grp.r2c(gin, gmid, stream=gs.cuda_stream)
-            grp.c2r(gmid, gout, stream=gs.cuda_stream)
-        for _ in range(3):
-            gstep()
-        reps = 50
-        gms = time_steps(gstep, gs, reps) / reps
-    gbytes = sum(2 * 4 * (4 * a0 * a1 * a2 + 40 * a0 * a1 * (a2 // 2 + 1)) for (a0, a1, a2) in gdims)
-    out["grouped_uneven"] = {"us_per_r2c_c2r": gms * 1e3, "gbs_passes_run": gbytes / (gms * 1e-3) / 1e9,
-                             "sizes": [f"{a}^3" for (a, _, _) in gdims], "fields_per_size": 4,
-                             "launches": fft3d.fft3d_group_launches(grp.handle, -1)
-                             + fft3d.fft3d_group_launches(grp.handle, 1), "graphs_per_step": 2}
+    reps = 50
+
+    def gtime(f):
+        with torch.cuda.stream(gs):
+            for _ in range(3):
+                f()
+            return time_steps(f, gs, reps) / reps
+
+    rec = {"sizes": [f"{a}^3" for (a, _, _) in gdims], "fields_per_size": 4}
+    forms = {"work_table": fft3d.FFT3D_GROUP_WORK_TABLE, "streams": fft3d.FFT3D_GROUP_STREAMS}
+    for name, form in forms.items():
+        grp.form = form
+        if form == fft3d.FFT3D_GROUP_STREAMS:
+            for i in range(len(gdims)):  # the streams form runs the per-size plans' autotuned shapes
+                fft3d.fft3d_autotune(fft3d.fft3d_group_plan_at(grp.handle, i), gin[i].data_ptr(),
+                                     gmid[i].data_ptr(), 3, sptr)
+        t_rt = gtime(lambda: grp.r2c_c2r(gin, gmid, gout, stream=gs.cuda_stream))
+        t_two = gtime(lambda: (grp.r2c(gin, gmid, stream=gs.cuda_stream),
+                               grp.c2r(gmid, gout, stream=gs.cuda_stream)))
+        rec[name] = {"us_per_r2c_c2r": t_rt * 1e3, "gbs_passes_run": gbytes / (t_rt * 1e-3) / 1e9,
+                     "us_per_r2c_then_c2r_calls": t_two * 1e3,
+                     "launches_per_step": fft3d.fft3d_group_launches(grp.handle, 0), "graphs_per_step": 1}
+    st = fft3d.fft3d_group_query_device_status(grp.handle, gs.cuda_stream)
+    rec["status_ok"] = st == fft3d.FFT3D_OK
+    best = min(forms, key=lambda k: rec[k]["us_per_r2c_c2r"])
+    rec["us_per_r2c_c2r"] = rec[best]["us_per_r2c_c2r"]
+    rec["faster_form"] = best
+    out["grouped_uneven"] = rec
     grp.close()
     del grp, gin, gmid, gout
     torch.cuda.empty_cache()

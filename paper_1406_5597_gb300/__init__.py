@@ -44,6 +44,10 @@ FFT3D_FLAG_CLUSTER_PLANE = 0x40
 FFT3D_FLAG_PADDED_REAL = 0x80
 FFT3D_FLAG_PRESERVE_INPUT = 0x100
 
+FFT3D_GROUP_STREAMS = 0
+FFT3D_GROUP_WORK_TABLE = 1
+FFT3D_GROUP_WORK_TABLE_TEST_STALL = 2
+
 _lib = None
 _lock = threading.Lock()
 
@@ -91,7 +95,11 @@ _SIGS = {
     "fft3d_group_plan_at": ([_P, _I], _P),
     "fft3d_group_r2c": ([_P, _P, _P, _P], _I),
     "fft3d_group_c2r": ([_P, _P, _P, _P], _I),
+    "fft3d_group_r2c_c2r": ([_P, _P, _P, _P, _P], _I),
     "fft3d_group_launches": ([_P, _I], _I),
+    "fft3d_group_set_form": ([_P, _I], _I),
+    "fft3d_group_get_form": ([_P], _I),
+    "fft3d_group_query_device_status": ([_P, _P], _I),
     "fft3d_group_destroy": ([_P], None),
 }
 
@@ -432,8 +440,25 @@ def fft3d_group_c2r(group, in_ptrs, out_ptrs, stream=0):
     return load().fft3d_group_c2r(_v(group), _ptr_array(in_ptrs), _ptr_array(out_ptrs), _v(stream))
 
 
+def fft3d_group_r2c_c2r(group, in_ptrs, mid_ptrs, out_ptrs, stream=0):
+    return load().fft3d_group_r2c_c2r(_v(group), _ptr_array(in_ptrs), _ptr_array(mid_ptrs), _ptr_array(out_ptrs),
+                                      _v(stream))
+
+
 def fft3d_group_launches(group, direction=-1):
     return load().fft3d_group_launches(_v(group), direction)
+
+
+def fft3d_group_set_form(group, form):
+    return load().fft3d_group_set_form(_v(group), form)
+
+
+def fft3d_group_get_form(group):
+    return load().fft3d_group_get_form(_v(group))
+
+
+def fft3d_group_query_device_status(group, stream=0):
+    return load().fft3d_group_query_device_status(_v(group), _v(stream))
 
 
 def fft3d_group_destroy(group):
@@ -465,6 +490,23 @@ class Group(_Closing):
         st = fft3d_group_c2r(self.handle, [t.data_ptr() for t in ins], [t.data_ptr() for t in outs], stream)
         if st != FFT3D_OK:
             raise Fft3dError(st, "fft3d_group_c2r")
+
+    def r2c_c2r(self, ins, mids, outs, stream=0):
+        """Forward of ins into mids, then inverse of mids (clobbered) into outs, in one call."""
+        st = fft3d_group_r2c_c2r(self.handle, [t.data_ptr() for t in ins], [t.data_ptr() for t in mids],
+                                 [t.data_ptr() for t in outs], stream)
+        if st != FFT3D_OK:
+            raise Fft3dError(st, "fft3d_group_r2c_c2r")
+
+    @property
+    def form(self):
+        return fft3d_group_get_form(self.handle)
+
+    @form.setter
+    def form(self, value):
+        st = fft3d_group_set_form(self.handle, value)
+        if st != FFT3D_OK:
+            raise Fft3dError(st, "fft3d_group_set_form")
 
     def close(self):
         if self.handle:
