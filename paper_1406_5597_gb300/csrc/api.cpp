@@ -183,8 +183,8 @@ struct Axis {
     const TcEntry* tc = nullptr;  // tensor-core radix-16 column kernel (TC dtypes)
     const SplitEntry* split[2] = {nullptr, nullptr};  // cluster-split column kernels of this length
     const TmaSplitEntry* tsplit = nullptr;             // TMA-fed cluster split of this length
-    const L2SplitEntry* l2split = nullptr;             // residue split through L2 of this length (n0 axis)
-    float2* d_l2scratch = nullptr;                     // its scratch (plan-owned), for l2_ctas CTAs
+    const L2SplitEntry* l2split = nullptr;             // residue split through L2 of this length
+    float2* d_l2scratch = nullptr;                     // its scratch (the plan's, shared by both axes)
     int l2_ctas = 0;
     GenPlan gen{};
     float2* d_tw = nullptr;
@@ -386,20 +386,26 @@ cudaError_t run_l2split(const Axis& a, int dir, const ColArgs& ca, cudaStream_t 
 {
     SplitMaps maps{};
     const int C = a.l2split->C;
+    const bool shift = ca.S & 1;  // odd stride: odd residues' rows start one value early, boxes 2 wider
     for (int r = 0; r < C; ++r) {
-        const cudaError_t e = encode_tensor_map_2d(&maps.map[r], ca.data + r * ca.S, 2ull * ca.C,
-                                                   (unsigned long long)ca.nb * (a.L / C), 8ull * C * ca.S, 32, 256);
+        const long long rs = r * ca.S;
+        const int off = shift ? (int)(rs & 1) : 0;
+        const cudaError_t e = encode_tensor_map_2d(&maps.map[r], ca.data + rs - off, 2ull * (ca.C + off),
+                                                   (unsigned long long)ca.nb * (a.L / C), 8ull * C * ca.S,
+                                                   shift ? 36u : 32u, 256);
         if (e != cudaSuccess) return e;
     }
-    return dir < 0 ? a.l2split->fwd(ca, maps, a.d_l2scratch, a.l2_ctas, s)
-                   : a.l2split->inv(ca, maps, a.d_l2scratch, a.l2_ctas, s);
+    const ColL2SplitFn f = shift ? (dir < 0 ? a.l2split->fwd_shift : a.l2split->inv_shift)
+                                 : (dir < 0 ? a.l2split->fwd : a.l2split->inv);
+    return f(ca, maps, a.d_l2scratch, a.l2_ctas, s);
 }
 
-// The residue split through L2 applies to the n0 pass of the plan it was set up for.
+// The residue split applies to a column pass whose batch entries are stacked
+// at L S, with at least 16 columns, and an even stride or the shifted form.
 bool l2split_ok(const Axis& a, const ColArgs& ca)
 {
-    return a.l2split && a.d_l2scratch && ca.S % 2 == 0 && ca.Bs == (long long)a.L * ca.S && ca.C >= 16 &&
-           ((uintptr_t)ca.data & 15) == 0;
+    return a.l2split && a.d_l2scratch && (ca.S % 2 == 0 || a.l2split->fwd_shift) && ca.Bs == (long long)a.L * ca.S &&
+           ca.C >= 16 && ((uintptr_t)ca.data & 15) == 0;
 }
 
 cudaError_t run_tma_split(const Axis& a, int dir, const ColArgs& ca, cudaStream_t s)
@@ -489,6 +495,7 @@ struct fft3d_plan_s {
     // kernels, rows per CTA of the row kernels (0: compiled default), and
     // whether the n0 pass may use the TMA kernel
     int choice_w0 = 0, choice_w1 = 0, choice_rows = 0, choice_tma = 1, choice_tma1 = 1;
+    float2* d_l2scratch = nullptr;  // the residue-split column kernels' scratch (both axes)
     void* workspace = nullptr;
     std::string desc;
     bool profiling = false;
@@ -526,8 +533,8 @@ void free_plan(fft3d_plan_s* p)
         cudaFree(a->d_blu);
         cudaFree(a->d_tw64);
         cudaFree(a->d_blu64);
-        cudaFree(a->d_l2scratch);
     }
+    cudaFree(p->d_l2scratch);
     cudaFree(p->d_twpack64);
     cudaFree(p->d_twpack);
     cudaFree(p->d_status);
@@ -702,7 +709,7 @@ std::string axis_desc(const fft3d_plan_s* p, const Axis& a, bool row)
                            : a.spec->row_rows;
         std::snprintf(b, sizeof b, "L=%d E=%d rows/CTA=%d %s", a.L, a.spec->row_E, rr,
                       a.spec->row_warp ? "warp" : "smem");
-    } else if (&a == &p->ax0 && p->choice_tma == 5 && a.l2split) {
+    } else if (((&a == &p->ax0) ? p->choice_tma : p->choice_tma1) == 5 && a.l2split) {
         std::snprintf(b, sizeof b, "L=%d E=32 cols/CTA=16 tma-residue-split C=%d via L2", a.L, a.l2split->C);
     } else if (((&a == &p->ax0) ? p->choice_tma : p->choice_tma1) == 4 && a.tsplit &&
                (&a == &p->ax0 ? p->P % 2 == 0 && p->P >= 16 : p->H % 2 == 0 && p->H >= 16)) {
@@ -910,17 +917,15 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
             find_split(a.L, a.split);
             a.tsplit = find_tma_split(a.L);
         }
-        if (a.spec && i == 0 && p->P % 2 == 0 && p->P >= 16 && dtype == FFT3D_F32 &&
-            !(flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE)) {
-            // the residue split of the n0 pass and its scratch (one region per resident CTA)
-            if (const L2SplitEntry* le = find_l2split(a.L)) {
-                a.l2_ctas = le->ctas();
-                const size_t bytes = le->scratch_values(a.l2_ctas) * sizeof(float2);
-                if (a.l2_ctas > 0 && cudaMalloc((void**)&a.d_l2scratch, bytes) == cudaSuccess) a.l2split = le;
-                else a.l2_ctas = 0;
-                cudaGetLastError();  // a failed allocation only leaves the form out
-            }
-        }
+        // the residue split of a column pass: an axis stride of at least 16
+        // columns, even, or odd where the length has the shifted form
+        const long long stride = i == 0 ? p->P : p->H;
+        if (a.spec && i < 2 && stride >= 16 && dtype == FFT3D_F32 && !(flags & FFT3D_FLAG_EXPLICIT_TRANSPOSE))
+            if (const L2SplitEntry* le = find_l2split(a.L))
+                if (stride % 2 == 0 || le->fwd_shift) {
+                    a.l2split = le;
+                    a.l2_ctas = le->ctas();
+                }
         a.gen = generic_radices(a.L);
         if (upload(forward_table(a.L, a.L), &a.d_tw) != cudaSuccess ||
             (!smooth2357(a.L) && setup_bluestein(a) != cudaSuccess) ||
@@ -928,6 +933,21 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
             free_plan(p);
             fail(FFT3D_ERR_ALLOC);
             return nullptr;
+        }
+    }
+    {
+        // the residue split's scratch: one region per resident CTA, shared by
+        // both axes (a plan's passes run one after another on its stream)
+        size_t bytes = 0;
+        for (Axis* a : {&p->ax0, &p->ax1})
+            if (a->l2split && a->l2_ctas > 0)
+                bytes = std::max(bytes, a->l2split->scratch_values(a->l2_ctas) * sizeof(float2));
+        float2* scratch = nullptr;
+        if (bytes && cudaMalloc((void**)&scratch, bytes) == cudaSuccess) p->d_l2scratch = scratch;
+        cudaGetLastError();  // a failed allocation only leaves the form out
+        for (Axis* a : {&p->ax0, &p->ax1}) {
+            if (!p->d_l2scratch || a->l2_ctas <= 0) a->l2split = nullptr;
+            a->d_l2scratch = a->l2split ? p->d_l2scratch : nullptr;
         }
     }
     // default n0-pass kernel: the plain kernel for long n0 axes, whose rows lie
@@ -1637,8 +1657,9 @@ int fft3d_autotune(fft3d_handle p, float* real, void* cplx, int reps, void* stre
             if (t < best) best = t, pick = w, pick_tma = 0;
         }
         p->choice_w1 = pick;
-        for (int f = 2; f <= 4; ++f) {  // cluster-split kernels, plain and TMA-fed
-            if (f < 4 ? !p->ax1.split[f - 2] : (!p->ax1.tsplit || H % 2 || H < 16)) continue;
+        for (int f = 2; f <= 5; ++f) {  // split kernels: cluster (plain, TMA-fed), residues through L2
+            if (f < 4 ? !p->ax1.split[f - 2] : f == 4 ? (!p->ax1.tsplit || H % 2 || H < 16) : !p->ax1.l2split)
+                continue;
             p->choice_tma1 = f;
             const float t = time_pass([&] { run_col(p, p->ax1, -1, X, H, H, B * n0, n1 * H, s); }, reps, s);
             if (t < best) best = t, pick_tma = f;

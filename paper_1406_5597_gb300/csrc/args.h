@@ -174,6 +174,7 @@ using ColL2SplitFn = cudaError_t (*)(const ColArgs&, const SplitMaps&, float2* s
 struct L2SplitEntry {
     int L, C;
     ColL2SplitFn fwd, inv;
+    ColL2SplitFn fwd_shift, inv_shift;  // odd axis stride (even C only; else nullptr)
     size_t (*scratch_values)(int ctas);
     int (*ctas)();  // grid size on the current device (resident CTAs)
 };

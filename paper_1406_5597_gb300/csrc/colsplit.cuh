@@ -380,13 +380,19 @@ inline cudaError_t launch_col_tma_split(const ColArgs& a, const SplitMaps& maps,
 // copies, bounded, and ends).
 // Requirements (checked by the host): P even, Bs = L*P, at least 16 columns.
 // ---------------------------------------------------------------------------
-template <int C, bool PARK>
+// SHIFT: an odd axis stride S (the n1 pass, S = n2/2 + 1): the rows of an odd
+// residue start 8 bytes past a 16-byte boundary, so their tensor map starts
+// one complex value early, and every box is two columns wider (WS = W + 2),
+// the thread reading its column at offset (r S) mod 2.
+template <int C, bool PARK, bool SHIFT = false>
 struct L2SplitGeom {
     static constexpr int L = kSplitLC * C;
     static constexpr int T = kSplitLC / kSplitE;  // 16 threads per column
     static constexpr int NT = kSplitW * T;         // 256 threads
     static constexpr int STAGES = 2;
-    static constexpr unsigned SUB_BYTES = (unsigned)kSplitLC * kSplitW * sizeof(float2);  // 64 KB
+    static constexpr int WS = SHIFT ? kSplitW + 2 : kSplitW;                          // slot row width
+    static constexpr unsigned SUB_BYTES = (unsigned)kSplitLC * WS * sizeof(float2);  // 64 / 72 KB
+    static_assert(!SHIFT || C % 2 == 0, "an odd stride needs an even C for 16-byte row strides");
     // PARK: residue C-2 is parked in shared memory next to the ring, the
     // others (0 .. C-3, or 0 .. C-2 without PARK) in L2 scratch
     static constexpr int NL2 = PARK ? C - 2 : C - 1;  // residues parked in L2
@@ -394,18 +400,17 @@ struct L2SplitGeom {
     static constexpr size_t scratch_per_cta = (size_t)(NL2 > 0 ? NL2 : 1) * kSplitLC * kSplitW;  // float2 values
 };
 
-template <int C, int DIR, bool PARK>
-__global__ void __launch_bounds__(L2SplitGeom<C, PARK>::NT) col_l2split_kernel(const __grid_constant__ SplitMaps maps,
-                                                                              ColArgs a, float2* scratch,
-                                                                              long long ntiles)
+template <int C, int DIR, bool PARK, bool SHIFT = false>
+__global__ void __launch_bounds__(L2SplitGeom<C, PARK, SHIFT>::NT) col_l2split_kernel(
+    const __grid_constant__ SplitMaps maps, ColArgs a, float2* scratch, long long ntiles)
 {
-    using G = L2SplitGeom<C, PARK>;
-    constexpr int NL2 = G::NL2;
+    using G = L2SplitGeom<C, PARK, SHIFT>;
+    constexpr int NL2 = G::NL2, WS = G::WS;
     constexpr int L = G::L, LC = kSplitLC, E = kSplitE, W = kSplitW, T = G::T, STAGES = G::STAGES;
     constexpr int BOXR = 256, NBOX = LC / BOXR;
     extern __shared__ __align__(1024) unsigned char smraw[];
     float2* ring = reinterpret_cast<float2*>(smraw);
-    float2* park = ring + (size_t)STAGES * LC * W;  // PARK: residue C-2 (each thread's own positions)
+    float2* park = ring + (size_t)STAGES * LC * WS;  // PARK: residue C-2 (each thread's own positions)
     unsigned long long* bars =
         reinterpret_cast<unsigned long long*>(smraw + (size_t)(STAGES + (PARK ? 1 : 0)) * G::SUB_BYTES);
     const int c = threadIdx.x, t = threadIdx.y;
@@ -431,10 +436,10 @@ __global__ void __launch_bounds__(L2SplitGeom<C, PARK>::NT) col_l2split_kernel(c
         const long long b = tile / ctiles;
         const long long c0 = (tile - b * ctiles) * W;
         mbar_arrive_expect_tx(&bars[s], G::SUB_BYTES);
-        float2* slot = ring + (size_t)s * LC * W;
+        float2* slot = ring + (size_t)s * LC * WS;
 #pragma unroll
         for (int k = 0; k < NBOX; ++k)
-            tma_load_2d(slot + (size_t)k * BOXR * W, &maps.map[r], (int)(2 * c0), (int)(b * LC + k * BOXR), &bars[s]);
+            tma_load_2d(slot + (size_t)k * BOXR * WS, &maps.map[r], (int)(2 * c0), (int)(b * LC + k * BOXR), &bars[s]);
         ++n_issued;
     };
 
@@ -455,11 +460,12 @@ __global__ void __launch_bounds__(L2SplitGeom<C, PARK>::NT) col_l2split_kernel(c
         const long long b = tile / ctiles;
         const long long c0 = (tile - b * ctiles) * W;
         const bool active = (c0 + c) < a.C;
-        float2* buf = ring + (size_t)s * LC * W;
+        float2* buf = ring + (size_t)s * LC * WS;
+        const int off = SHIFT ? (int)((r * a.S) & 1) : 0;  // the odd residues' maps start one value early
         float2 v[E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = buf[(t + T * m) * W + c];
-        __syncthreads();  // the slot now serves as the exchange buffer
+        for (int m = 0; m < E; ++m) v[m] = buf[(t + T * m) * WS + c + off];
+        __syncthreads();  // the slot now serves as the exchange buffer (W-wide rows from here on)
         // (twiddles from the table: registers go to the combine's loads below)
         fft_group<LC, E, DIR, C>(v, t, a.tw, ColExchange{buf, W, c});
         if (r > 0) {
@@ -530,12 +536,12 @@ inline size_t l2split_scratch_values(int ctas)
     return (size_t)ctas * L2SplitGeom<C, PARK>::scratch_per_cta;
 }
 
-template <int C, int DIR, bool PARK>
+template <int C, int DIR, bool PARK, bool SHIFT = false>
 inline cudaError_t launch_col_l2split(const ColArgs& a, const SplitMaps& maps, float2* scratch, int ctas,
                                       cudaStream_t s)
 {
-    using G = L2SplitGeom<C, PARK>;
-    auto k = col_l2split_kernel<C, DIR, PARK>;
+    using G = L2SplitGeom<C, PARK, SHIFT>;
+    auto k = col_l2split_kernel<C, DIR, PARK, SHIFT>;
     static PerDevice limit;  // the shared memory limit, raised once per device
     cudaError_t e = smem_limit_per_device(limit, k, G::smem);
     if (e != cudaSuccess) return e;

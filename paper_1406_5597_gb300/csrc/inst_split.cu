@@ -44,14 +44,18 @@ int l2split_ctas()
 
 #define FFT3D_L2SPLIT(L, C, PARK)                                                                       \
     { L, C, &launch_col_l2split<C, -1, PARK>, &launch_col_l2split<C, 1, PARK>,                          \
+      &launch_col_l2split<C, -1, false, true>, &launch_col_l2split<C, 1, false, true>,                  \
+      &l2split_scratch_values<C, PARK>, &l2split_ctas<C, PARK> }
+#define FFT3D_L2SPLIT_NOSHIFT(L, C, PARK)                                                               \
+    { L, C, &launch_col_l2split<C, -1, PARK>, &launch_col_l2split<C, 1, PARK>, nullptr, nullptr,        \
       &l2split_scratch_values<C, PARK>, &l2split_ctas<C, PARK> }
 
 const L2SplitEntry* l2split_entries(int* n)
 {
     static const L2SplitEntry e[] = {
-        FFT3D_L2SPLIT(1024, 2, false),  // the other residue in L2
-        FFT3D_L2SPLIT(1536, 3, true),   // residue 1 in shared memory, residue 0 in L2
-        FFT3D_L2SPLIT(2048, 4, false),  // residues 0 .. 2 in L2
+        FFT3D_L2SPLIT(1024, 2, false),          // the other residue in L2
+        FFT3D_L2SPLIT_NOSHIFT(1536, 3, true),   // residue 1 in shared memory, residue 0 in L2
+        FFT3D_L2SPLIT(2048, 4, false),          // residues 0 .. 2 in L2
     };
     *n = (int)(sizeof(e) / sizeof(e[0]));
     return e;

@@ -103,12 +103,16 @@ CASES = [
     ((2048, 3, 10), 2, "f32", "l2split"),       # residue split through L2 scratch, C = 4, ragged, batch
     ((1536, 2, 30), 1, "f32", "l2split"),       # C = 3
     ((1024, 4, 12), 1, "f32", "l2split"),       # C = 2
+    ((2, 2048, 40), 1, "f32", "l2split_n1"),    # the n1 pass, odd H: odd residues' boxes shifted, C = 4
+    ((3, 1024, 36), 2, "f32", "l2split_n1"),    # the n1 pass, odd H, C = 2, batch
+    ((2, 2048, 30), 1, "f32", "l2split_n1"),    # the n1 pass, even H
 ]
 
 
 # column-form choices {w0, w1, rows, form0, form1} of the split cases
 SPLIT_CHOICES = {"split0": [0, 0, 0, 2, 0], "split1": [0, 0, 0, 3, 0], "split0_n1": [0, 0, 0, 0, 2],
-                 "tsplit": [0, 0, 0, 4, 0], "tsplit_n1": [0, 0, 0, 0, 4], "l2split": [0, 0, 0, 5, 0]}
+                 "tsplit": [0, 0, 0, 4, 0], "tsplit_n1": [0, 0, 0, 0, 4], "l2split": [0, 0, 0, 5, 0],
+                 "l2split_n1": [0, 0, 0, 0, 5]}
 
 
 def _flags(lib, name):

@@ -806,14 +806,16 @@ def test_long_axis_column_forms_match_oracle(cuda_lib, shape):
 @pytest.mark.parametrize("shape,batch", [((2048, 2, 6), 1), ((1024, 3, 10), 1), ((1536, 4, 12), 1),
                                          ((2, 2048, 32), 1), ((3, 1024, 30), 1), ((1024, 2, 8), 2),
                                          ((2048, 3, 4), 2), ((2048, 3, 10), 1), ((1024, 4, 12), 2),
-                                         ((1536, 2, 30), 1), ((2, 2048, 30), 1)],
+                                         ((1536, 2, 30), 1), ((2, 2048, 30), 1), ((3, 1024, 36), 2),
+                                         ((2, 2048, 40), 1)],
                          ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else f"b{v}")
 def test_cluster_split_column_forms_match_oracle(cuda_lib, shape, batch):
     """The cluster-split column kernels (forms 2 and 3 of the n0 and n1
     passes: the tile's rows split by residue over a 2- or 4-CTA cluster, the
     final radix-C step through distributed shared memory; form 4: the same
     split with 512-row TMA-fed sub-transforms on 2, 3 or 4 CTAs; form 5: the
-    512-row residues of one CTA's tile, parked in L2 scratch) give the
+    512-row residues of one CTA's tile, parked in L2 scratch, on the n1 axis
+    with the odd-stride shift) give the
     oracle's transform in both directions: ragged column tiles, batches, the
     n1 axis, and the input-preserving inverse (its first pass writes
     elsewhere)."""
@@ -830,7 +832,7 @@ def test_cluster_split_column_forms_match_oracle(cuda_lib, shape, batch):
     for flags in (0, lib.FFT3D_FLAG_PRESERVE_INPUT):
         plan = lib.Plan(n0, n1, n2, lib.FFT3D_F32, batch, flags)
         for f0 in (0, 2, 3, 4, 5):
-            for f1 in (0, 2, 3, 4):
+            for f1 in (0, 2, 3, 4, 5):
                 if f0 < 2 and f1 < 2:
                     continue
                 if lib.fft3d_set_choices(plan.handle, [0, 0, 0, f0, f1]) != lib.FFT3D_OK:
