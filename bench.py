@@ -56,6 +56,19 @@ SEED_512 = 1408
 REF_SAMPLE_MAX = 512
 
 
+def nonlinear_bytes(m):
+    """Bytes the nonlinear term at m^3 moves as run (one read + one write per
+    pass of what it touches): the inverse n0 and n1 passes of the three
+    fields (16 M bytes each), the fused rows (3 half spectra in, 6 out), the
+    forward n1 pass of the six products over the kept k2 only, and their
+    forward n0 pass over the columns whose k1 and k2 are both kept."""
+    H = m // 2 + 1
+    M = m * m * H
+    keep2 = (m + 2) // 3
+    keep1 = (m + 2) // 3 + (m - 1) // 3
+    return int(2 * 3 * 16 * M + (3 + 6) * 8 * M + 6 * 16 * M * keep2 / H + 6 * 16 * M * keep2 / H * keep1 / m)
+
+
 def two_pass_bytes(n0, n1, n2):
     N = n0 * n1 * n2
     M = n0 * n1 * (n2 // 2 + 1)
@@ -696,7 +709,7 @@ def pseudo_spectral(ctx):
             nl(U, out=prod, stream=ns_)
         reps = 50
         nms = time_steps(lambda: nl(U, out=prod, stream=ns_), ns_, reps) / reps
-    run_bytes = 360 * Mc  # bytes of the five passes as run (3+3 inverse, 6+6 forward, fused rows)
+    run_bytes = nonlinear_bytes(m)  # bytes of the five passes as run
     out["nonlinear_256"] = {"ms_per_application": nms, "gbs_passes_run": run_bytes / (nms * 1e-3) / 1e9,
                             "passes_run_bytes": run_bytes, "launches": fft3d.fft3d_nonlinear_launches(nl.handle),
                             "graph": True}
@@ -716,7 +729,7 @@ def pseudo_spectral(ctx):
     # u* and the accumulator out (stage 1); u*, products, accumulator in, u out (stage 2)
     kept = (2 * ((m - 1) // 3) + 1) ** 2 * ((m - 1) // 3 + 1)
     f = kept / Mc
-    run_bytes = int(2 * 360 * Mc + 8 * Mc * ((3 + 6 * f + 6) + (3 + 6 * f + 3 + 3)))
+    run_bytes = int(2 * nonlinear_bytes(m) + 8 * Mc * ((3 + 6 * f + 6) + (3 + 6 * f + 3 + 3)))
     out["navier_stokes_256"] = {"ms_per_step": sms, "gbs_passes_run": run_bytes / (sms * 1e-3) / 1e9,
                                 "passes_run_bytes": run_bytes, "launches": fft3d.fft3d_ns_launches(ns.handle),
                                 "graph": True, "scheme": "Heun RK2, nu = 0.01, dt = 1e-3"}

@@ -636,6 +636,19 @@ cudaError_t launch_col_args(fft3d_plan_s* p, const Axis& a, int dir, const ColAr
     if (a.L <= 1) {  // length-1 axis: the transform is the identity (apart from scale / mask / destination)
         if (!ca.dst && ca.scale == 1.0f) return cudaSuccess;
     }
+    if (ca.nb2 > 1 && (uses_generic(p, a, false) || a.tc || !a.spec)) {
+        // an outer batch on a path without it: one pass per group
+        for (long long b2 = 0; b2 < ca.nb2; ++b2) {
+            ColArgs c = ca;
+            c.data += b2 * ca.Bs2;
+            if (c.dst) c.dst += b2 * ca.Bs2;
+            c.nb2 = 1;
+            c.Bs2 = 0;
+            const cudaError_t e = launch_col_args(p, a, dir, c, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     if (a.tc) {  // tensor-core radix-16 stages
         if (p->dtype == FFT3D_F32_TC_BF16X3)
             return dir < 0 ? a.tc->bf16_fwd(ca, p->d_tcg, s) : a.tc->bf16_inv(ca, p->d_tcg, s);
@@ -643,6 +656,10 @@ cudaError_t launch_col_args(fft3d_plan_s* p, const Axis& a, int dir, const ColAr
     }
     if (uses_generic(p, a, false)) return generic_col(ca, a.gen, dir, s);
     const bool n0axis = (&a == &p->ax0);
+    if (ca.nb2 > 1) {  // an outer batch: the plain column kernel is the form that takes it
+        const int w = n0axis ? p->choice_w0 : p->choice_w1;
+        return dir < 0 ? a.spec->col_fwd(ca, w, s) : a.spec->col_inv(ca, w, s);
+    }
     const int form = n0axis ? p->choice_tma : p->choice_tma1;
     if (form == 4 && tma_split_ok(a, ca)) return run_tma_split(a, dir, ca, s);  // TMA-fed cluster split
     if (form == 5 && l2split_ok(a, ca)) return run_l2split(a, dir, ca, s);     // residue split through L2
@@ -1317,14 +1334,26 @@ cudaError_t enqueue_nonlinear(fft3d_nl_s* nl, const void* uhat, void* nhat, cuda
     // 3. rows: three c2r, six products, six r2c with the 2/3 rule on k2
     NlRowArgs r{W, Nh, n0 * n1, M, p->ax2.d_tw, p->d_twpack, (p->n2 + 2) / 3};
     if ((e = p->ax2.spec->nl(r, s)) != cudaSuccess) return e;
+    // The forward passes visit only what the 2/3 rule keeps; everything else
+    // is zero already.  The rows wrote zeros at k2 >= keep2, so the n1 pass
+    // transforms the columns k2 < keep2 alone (a column of zeros stays zero)
+    // and zeroes the k1 the rule drops; the n0 pass then transforms only the
+    // columns whose k1 and k2 are both kept (two blocks of k1: 0 .. A-1 and
+    // n1-B .. n1-1), the others being zero in place.
+    const long long keep2 = (p->n2 + 2) / 3;
     // 4. n1 forward of the six products, 2/3 rule on k1
-    {
-        ColArgs c{Nh, H, H, 6 * n0, n1 * H, p->ax1.d_tw, 1.0f, p->d_status, nullptr, 1};
+    if (p->n1 > 1) {
+        ColArgs c{Nh, H, keep2, 6 * n0, n1 * H, p->ax1.d_tw, 1.0f, p->d_status, nullptr, 1};
         if ((e = launch_col_args(p, p->ax1, -1, c, s)) != cudaSuccess) return e;
     }
-    // 5. n0 forward, 2/3 rule on k0 and the 1/N normalisation
-    {
-        ColArgs c{Nh, P, P, 6, M, p->ax0.d_tw, 1.0f / (float)p->N, p->d_status, nullptr, 1};
+    // 5. n0 forward of the kept (k1, k2) columns, 2/3 rule on k0 and the 1/N normalisation
+    const long long A = (n1 + 2) / 3, B = (n1 - 1) / 3;  // kept k1 >= 0 (3 k1 < n1), kept k1 < 0 (3 |k1| < n1)
+    const long long starts[2] = {0, n1 - B}, counts[2] = {A, B};
+    for (int q = 0; q < 2; ++q) {
+        if (counts[q] <= 0 || (q == 1 && n1 == 1)) continue;
+        ColArgs c{Nh + starts[q] * H, P, keep2, counts[q], H, p->ax0.d_tw, 1.0f / (float)p->N, p->d_status, nullptr, 1};
+        c.nb2 = 6;
+        c.Bs2 = M;
         if ((e = launch_col_args(p, p->ax0, -1, c, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -18,6 +18,9 @@ struct ColArgs {
     int* status;         // device status word (bounded waits that give up set bits here)
     float2* dst;         // result goes here (same layout) instead of in place; nullptr: in place
     int mask23;          // nonzero: zero the outputs whose signed index k has 3|k| >= L (2/3 rule)
+    // outer batch (plain column kernel only): nb2 groups of the nb entries, group stride Bs2
+    long long nb2 = 1;
+    long long Bs2 = 0;
 };
 
 // Output factor of a column pass for output index k of a length-L axis:

@@ -36,10 +36,12 @@ __global__ void __launch_bounds__(MAXT) col_kernel(ColArgs a, int W)
     const int c = threadIdx.x;
     const int t = threadIdx.y;
     const long long ctiles = (a.C + W - 1) / W;
-    const long long b = blockIdx.x / ctiles;
-    const long long c0 = (blockIdx.x - b * ctiles) * W;
+    const long long bb = blockIdx.x / ctiles;  // batch entry b of group b2
+    const long long c0 = (blockIdx.x - bb * ctiles) * W;
+    const long long b2 = bb / a.nb, b = bb - b2 * a.nb;
+    const long long boff = b2 * a.Bs2 + b * a.Bs;
     const bool active = (c0 + c) < a.C;
-    float2* base = a.data + b * a.Bs + c0 + c;
+    float2* base = a.data + boff + c0 + c;
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m)
@@ -47,7 +49,7 @@ __global__ void __launch_bounds__(MAXT) col_kernel(ColArgs a, int W)
     ColExchange ex{sm, W, c};
     fft_group<L, E, DIR>(v, t, a.tw, ex);
     if (active) {
-        float2* out = (a.dst ? a.dst : a.data) + b * a.Bs + c0 + c;
+        float2* out = (a.dst ? a.dst : a.data) + boff + c0 + c;
         if (a.mask23 == 0 && a.scale == 1.0f) {
 #pragma unroll
             for (int m = 0; m < E; ++m) out[(long long)(t + T * m) * a.S] = v[m];
@@ -690,7 +692,7 @@ inline cudaError_t launch_col(const ColArgs& a, int w, cudaStream_t s)
         cudaError_t e = smem_limit_per_device(limit, k, smem_max);
         if (e != cudaSuccess) return e;
     }
-    const long long tiles = a.nb * ((a.C + wr - 1) / wr);
+    const long long tiles = a.nb2 * a.nb * ((a.C + wr - 1) / wr);
     if (tiles <= 0) return cudaSuccess;
     k<<<(unsigned)tiles, dim3(wr, T), smem, s>>>(a, wr);
     return cudaGetLastError();
