@@ -332,10 +332,14 @@ void fft3d_group_destroy(fft3d_group_handle group);
  *     ij in (00, 01, 02, 11, 12, 22) (in that order),
  * mask = the 2/3 rule: keep bin k iff 3|k_a| < n_a on every axis, with k_a the
  * signed wavenumber in [-n_a/2, n_a/2) (Nyquist bins always dropped).
- * Five launches, batched over the fields: n0 inverse x3 (out of place into the
+ * Passes, batched over the fields: n0 inverse x3 (out of place into the
  * workspace), n1 inverse x3, one row kernel doing the three c2r, the six
  * products in registers and the six r2c (k2 part of the mask), n1 forward x6
- * (k1 part), n0 forward x6 (k0 part and 1/N).  On a non-default stream the
+ * over the columns k2 the mask keeps (k1 part), n0 forward x6 over the
+ * columns (k1, k2) it keeps (k0 part and 1/N); the skipped columns are zero.
+ * The three middle passes can run per chunk of planes j0 (so that a chunk's
+ * operands stay in L2 between them), on one stream or alternating between
+ * two (fft3d_nonlinear_set_chunking).  On a non-default stream the
  * sequence is captured once into a CUDA graph per (uhat, nhat, workspace) and
  * replayed; on the legacy default stream it is launched directly.
  * Supported when n2/2 has a warp-resident row kernel (n2/2 in 8..512 of the
@@ -355,7 +359,22 @@ int fft3d_nonlinear_set_workspace(fft3d_nl_handle nl, void* dev_ptr);
  * of uhat, nhat and the workspace may overlap. */
 int fft3d_nonlinear_exec(fft3d_nl_handle nl, const void* uhat, void* nhat, void* stream);
 
-/* Kernel launches per fft3d_nonlinear_exec. */
+/* Plane chunking of the middle passes (n1 inverse, rows, n1 forward): planes
+ * = planes j0 per chunk (0 or >= n0: one chunk, the passes over the whole
+ * fields); streams = 1, or 2 to alternate the chunks between the caller's
+ * stream and a second stream of the plan (graph-captured calls only; calls
+ * on the legacy default stream use one stream).  Drops the captured graph;
+ * INVALID_ARG for planes < 0 or streams outside 1..2.  The n1 passes of a
+ * chunk take the fields as an outer batch (the plain column kernel where the
+ * whole-field pass may take another form), so results can differ between
+ * chunkings by rounding.  get: the current setting. */
+int fft3d_nonlinear_set_chunking(fft3d_nl_handle nl, int planes, int streams);
+int fft3d_nonlinear_get_chunking(fft3d_nl_handle nl, int* planes, int* streams);
+
+/* Kernel launches per fft3d_nonlinear_exec: the kernel nodes of the captured
+ * graph once a call on a stream has captured one; before that, the count the
+ * plan's kernel forms give (the forward n0 pass is one launch per kept k1 block
+ * where the column path takes the six fields as an outer batch, else six). */
 int fft3d_nonlinear_launches(fft3d_nl_handle nl);
 
 /* NULL-safe; blocks on the device. */
@@ -394,7 +413,11 @@ int fft3d_ns_set_workspace(fft3d_ns_handle ns, void* dev_ptr);
  * not overlap the workspace. */
 int fft3d_ns_step(fft3d_ns_handle ns, void* uhat, float nu, float dt, void* stream);
 
-/* Kernel launches per fft3d_ns_step. */
+/* The chunking of the step's nonlinear terms (as fft3d_nonlinear_set_chunking;
+ * drops the step's captured graph). */
+int fft3d_ns_set_chunking(fft3d_ns_handle ns, int planes, int streams);
+
+/* Kernel launches per fft3d_ns_step (counted as for fft3d_nonlinear_launches). */
 int fft3d_ns_launches(fft3d_ns_handle ns);
 
 /* NULL-safe; blocks on the device. */

@@ -79,12 +79,15 @@ _SIGS = {
     "fft3d_nonlinear_set_workspace": ([_P, _P], _I),
     "fft3d_nonlinear_exec": ([_P, _P, _P, _P], _I),
     "fft3d_nonlinear_launches": ([_P], _I),
+    "fft3d_nonlinear_set_chunking": ([_P, _I, _I], _I),
+    "fft3d_nonlinear_get_chunking": ([_P, _P, _P], _I),
     "fft3d_nonlinear_destroy": ([_P], None),
     "fft3d_ns_plan": ([_I, _I, _I], _P),
     "fft3d_ns_workspace_bytes": ([_P], ctypes.c_size_t),
     "fft3d_ns_set_workspace": ([_P, _P], _I),
     "fft3d_ns_step": ([_P, _P, ctypes.c_float, ctypes.c_float, _P], _I),
     "fft3d_ns_launches": ([_P], _I),
+    "fft3d_ns_set_chunking": ([_P, _I, _I], _I),
     "fft3d_ns_destroy": ([_P], None),
     "fft3d_autotune": ([_P, _P, _P, _I, _P], _I),
     "fft3d_get_choices": ([_P, _P], _I),
@@ -270,6 +273,18 @@ def fft3d_nonlinear_launches(nl):
     return load().fft3d_nonlinear_launches(_v(nl))
 
 
+def fft3d_nonlinear_set_chunking(nl, planes, streams):
+    return load().fft3d_nonlinear_set_chunking(_v(nl), planes, streams)
+
+
+def fft3d_nonlinear_get_chunking(nl):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    st = load().fft3d_nonlinear_get_chunking(_v(nl), ctypes.byref(a), ctypes.byref(b))
+    if st != FFT3D_OK:
+        raise Fft3dError(st, "fft3d_nonlinear_get_chunking")
+    return a.value, b.value
+
+
 def fft3d_nonlinear_destroy(nl):
     load().fft3d_nonlinear_destroy(_v(nl))
 
@@ -361,6 +376,10 @@ def fft3d_ns_step(ns, uhat_ptr, nu, dt, stream=0):
 
 def fft3d_ns_launches(ns):
     return load().fft3d_ns_launches(_v(ns))
+
+
+def fft3d_ns_set_chunking(ns, planes, streams):
+    return load().fft3d_ns_set_chunking(_v(ns), planes, streams)
 
 
 def fft3d_ns_destroy(ns):

@@ -1307,11 +1307,21 @@ struct fft3d_nl_s {
     const void* g_uhat = nullptr;  // operands the graph was captured with
     void* g_nhat = nullptr;
     void* g_ws = nullptr;
+    // plane chunking of the middle passes (n1 inverse, rows, n1 forward): the
+    // planes j0 in chunks of `chunk`, each chunk's three passes back to back
+    // so their operands stay in L2; with streams = 2 alternate chunks run on a
+    // second stream (captured graphs only) so one chunk's passes fill the
+    // other's ramp-up and tail
+    int chunk = 0;  // planes per chunk (0: all n0 planes in one chunk)
+    int streams = 1;
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
 
-cudaError_t enqueue_nonlinear(fft3d_nl_s* nl, const void* uhat, void* nhat, cudaStream_t s)
+// s2: the second stream of the two-stream chunk order, or nullptr (one stream)
+cudaError_t enqueue_nonlinear(fft3d_nl_s* nl, const void* uhat, void* nhat, cudaStream_t s, cudaStream_t s2)
 {
     fft3d_plan_s* p = nl->plan;
     const long long H = p->H, n0 = p->n0, n1 = p->n1, M = p->M, P = p->P;
@@ -1326,25 +1336,48 @@ cudaError_t enqueue_nonlinear(fft3d_nl_s* nl, const void* uhat, void* nhat, cuda
     } else if ((e = cudaMemcpyAsync(W, U, 3 * M * sizeof(float2), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
         return e;
     }
-    // 2. n1 inverse of the three fields, in place
-    if (p->n1 > 1) {
-        ColArgs c{W, H, H, 3 * n0, n1 * H, p->ax1.d_tw, 1.0f, p->d_status, nullptr, 0};
-        if ((e = launch_col_args(p, p->ax1, +1, c, s)) != cudaSuccess) return e;
-    }
-    // 3. rows: three c2r, six products, six r2c with the 2/3 rule on k2
-    NlRowArgs r{W, Nh, n0 * n1, M, p->ax2.d_tw, p->d_twpack, (p->n2 + 2) / 3};
-    if ((e = p->ax2.spec->nl(r, s)) != cudaSuccess) return e;
     // The forward passes visit only what the 2/3 rule keeps; everything else
-    // is zero already.  The rows wrote zeros at k2 >= keep2, so the n1 pass
+    // is zero already.  The rows write zeros at k2 >= keep2, so the n1 pass
     // transforms the columns k2 < keep2 alone (a column of zeros stays zero)
     // and zeroes the k1 the rule drops; the n0 pass then transforms only the
     // columns whose k1 and k2 are both kept (two blocks of k1: 0 .. A-1 and
     // n1-B .. n1-1), the others being zero in place.
     const long long keep2 = (p->n2 + 2) / 3;
-    // 4. n1 forward of the six products, 2/3 rule on k1
-    if (p->n1 > 1) {
-        ColArgs c{Nh, H, keep2, 6 * n0, n1 * H, p->ax1.d_tw, 1.0f, p->d_status, nullptr, 1};
-        if ((e = launch_col_args(p, p->ax1, -1, c, s)) != cudaSuccess) return e;
+    // 2-4, per chunk of planes j0 (all fields of a plane together):
+    //   n1 inverse of the three fields, in place;
+    //   rows: three c2r, six products, six r2c with the 2/3 rule on k2;
+    //   n1 forward of the six products over k2 < keep2, 2/3 rule on k1.
+    const long long chunk = nl->chunk > 0 && nl->chunk < n0 ? nl->chunk : n0;
+    const bool two = s2 != nullptr && chunk < n0;
+    if (two) {
+        if ((e = cudaEventRecord(nl->ev_fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s2, nl->ev_fork, 0)) != cudaSuccess) return e;
+    }
+    for (long long j0 = 0, g = 0; j0 < n0; j0 += chunk, ++g) {
+        const long long cc = n0 - j0 < chunk ? n0 - j0 : chunk;
+        const long long off = j0 * n1 * H;
+        cudaStream_t sc = (two && (g & 1)) ? s2 : s;
+        // all planes in one chunk: the fields' planes are one evenly strided
+        // batch (field stride M = n0 planes), which every column form takes
+        const bool whole = cc == n0;
+        if (p->n1 > 1) {
+            ColArgs c{W + off, H, H, whole ? 3 * n0 : cc, n1 * H, p->ax1.d_tw, 1.0f, p->d_status, nullptr, 0};
+            c.nb2 = whole ? 1 : 3;
+            c.Bs2 = whole ? 0 : M;
+            if ((e = launch_col_args(p, p->ax1, +1, c, sc)) != cudaSuccess) return e;
+        }
+        NlRowArgs r{W + off, Nh + off, cc * n1, M, p->ax2.d_tw, p->d_twpack, (int)keep2};
+        if ((e = p->ax2.spec->nl(r, sc)) != cudaSuccess) return e;
+        if (p->n1 > 1) {
+            ColArgs c{Nh + off, H, keep2, whole ? 6 * n0 : cc, n1 * H, p->ax1.d_tw, 1.0f, p->d_status, nullptr, 1};
+            c.nb2 = whole ? 1 : 6;
+            c.Bs2 = whole ? 0 : M;
+            if ((e = launch_col_args(p, p->ax1, -1, c, sc)) != cudaSuccess) return e;
+        }
+    }
+    if (two) {
+        if ((e = cudaEventRecord(nl->ev_join, s2)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, nl->ev_join, 0)) != cudaSuccess) return e;
     }
     // 5. n0 forward of the kept (k1, k2) columns, 2/3 rule on k0 and the 1/N normalisation
     const long long A = (n1 + 2) / 3, B = (n1 - 1) / 3;  // kept k1 >= 0 (3 k1 < n1), kept k1 < 0 (3 |k1| < n1)
@@ -1357,6 +1390,68 @@ cudaError_t enqueue_nonlinear(fft3d_nl_s* nl, const void* uhat, void* nhat, cuda
         if ((e = launch_col_args(p, p->ax0, -1, c, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// The second stream of the two-stream chunk order (created on first use, on
+// the plan's device), or nullptr when the plan runs on one stream.
+cudaStream_t nl_second_stream(fft3d_nl_s* nl)
+{
+    if (nl->streams < 2) return nullptr;
+    if (!nl->s2) {
+        int cur = 0;
+        if (cudaGetDevice(&cur) != cudaSuccess) return nullptr;
+        if (cur != nl->plan->device && cudaSetDevice(nl->plan->device) != cudaSuccess) return nullptr;
+        cudaStream_t st = nullptr;
+        cudaEvent_t a = nullptr, b = nullptr;
+        const bool ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+                        cudaEventCreateWithFlags(&a, cudaEventDisableTiming) == cudaSuccess &&
+                        cudaEventCreateWithFlags(&b, cudaEventDisableTiming) == cudaSuccess;
+        if (cur != nl->plan->device) cudaSetDevice(cur);
+        if (!ok) {
+            if (st) cudaStreamDestroy(st);
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+            return nullptr;
+        }
+        nl->s2 = st;
+        nl->ev_fork = a;
+        nl->ev_join = b;
+    }
+    return nl->s2;
+}
+
+// Kernel nodes of a captured graph, or -1.
+int graph_kernel_nodes(cudaGraph_t g)
+{
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return -1;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return -1;
+    int k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess) return -1;
+        k += t == cudaGraphNodeTypeKernel;
+    }
+    return k;
+}
+
+// Launches enqueue_nonlinear issues with this plan's kernel forms: the n0
+// inverse pass; per chunk of planes the n1 inverse pass, the fused rows and
+// the n1 forward pass; the n0 forward pass over the two kept k1 blocks.  A
+// pass over an outer batch of fields is one launch where the axis' column
+// path takes the batch, else one per field.
+int nonlinear_launch_count(const fft3d_nl_s* nl)
+{
+    const fft3d_plan_s* p = nl->plan;
+    const long long n0 = p->n0, n1 = p->n1, A = (n1 + 2) / 3, B = (n1 - 1) / 3;
+    auto outer = [p](const Axis& a) { return !(uses_generic(p, a, false) || a.tc || !a.spec); };
+    const long long chunk = nl->chunk > 0 && nl->chunk < n0 ? nl->chunk : n0;
+    const long long chunks = (n0 + chunk - 1) / chunk;
+    const bool o1 = chunks == 1 || outer(p->ax1);
+    const long long mid = (n1 > 1) * (o1 ? 2 : 9) + 1;
+    const int blocks = (A > 0) + (B > 0 && n1 > 1);
+    return (int)((n0 > 1) + chunks * mid + blocks * (outer(p->ax0) ? 1 : 6));
 }
 
 void drop_graph(fft3d_nl_s* nl)
@@ -1415,13 +1510,14 @@ int fft3d_nonlinear_exec(fft3d_nl_handle nl, const void* uhat, void* nhat, void*
         overlaps(nhat, 6 * M8, nl->workspace, 3 * M8))
         return fail(FFT3D_ERR_INVALID_ARG);
     cudaStream_t s = (cudaStream_t)stream;
-    if (!s) {  // the legacy default stream cannot be captured: launch directly
-        return enqueue_nonlinear(nl, uhat, nhat, s) == cudaSuccess ? FFT3D_OK : fail(FFT3D_ERR_CUDA);
+    if (!s) {  // the legacy default stream cannot be captured: launch directly, on one stream
+        return enqueue_nonlinear(nl, uhat, nhat, s, nullptr) == cudaSuccess ? FFT3D_OK : fail(FFT3D_ERR_CUDA);
     }
     if (!(nl->exec && nl->g_uhat == uhat && nl->g_nhat == nhat && nl->g_ws == nl->workspace)) {
         drop_graph(nl);
+        cudaStream_t s2 = nl_second_stream(nl);
         if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
-        const cudaError_t e = enqueue_nonlinear(nl, uhat, nhat, s);
+        const cudaError_t e = enqueue_nonlinear(nl, uhat, nhat, s, s2);
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(s, &g);
         if (e != cudaSuccess || e2 != cudaSuccess || !g) {
@@ -1465,16 +1561,17 @@ void drop_ns_graph(fft3d_ns_s* ns)
     ns->g_ws = nullptr;
 }
 
-cudaError_t enqueue_ns_step(fft3d_ns_s* ns, float2* u, float nu, float dt, cudaStream_t s)
+// s2: as for enqueue_nonlinear
+cudaError_t enqueue_ns_step(fft3d_ns_s* ns, float2* u, float nu, float dt, cudaStream_t s, cudaStream_t s2)
 {
     const fft3d_plan_s* p = ns->nl->plan;
     const long long M = p->M;
     float2* w = (float2*)ns->workspace;
     NsArgs a{u, w, w + 3 * M, w + 6 * M, p->n0, p->n1, p->n2, (int)p->H, M, nu, dt};
     cudaError_t e;
-    if ((e = enqueue_nonlinear(ns->nl, u, w + 6 * M, s)) != cudaSuccess) return e;
+    if ((e = enqueue_nonlinear(ns->nl, u, w + 6 * M, s, s2)) != cudaSuccess) return e;
     if ((e = launch_ns_stage(a, 1, s)) != cudaSuccess) return e;
-    if ((e = enqueue_nonlinear(ns->nl, w, w + 6 * M, s)) != cudaSuccess) return e;
+    if ((e = enqueue_nonlinear(ns->nl, w, w + 6 * M, s, s2)) != cudaSuccess) return e;
     return launch_ns_stage(a, 2, s);
 }
 
@@ -1517,11 +1614,12 @@ int fft3d_ns_step(fft3d_ns_handle ns, void* uhat, float nu, float dt, void* stre
     if (overlaps(uhat, 3 * M8, ns->workspace, 15 * M8)) return fail(FFT3D_ERR_INVALID_ARG);
     cudaStream_t s = (cudaStream_t)stream;
     float2* u = (float2*)uhat;
-    if (!s) return enqueue_ns_step(ns, u, nu, dt, s) == cudaSuccess ? FFT3D_OK : fail(FFT3D_ERR_CUDA);
+    if (!s) return enqueue_ns_step(ns, u, nu, dt, s, nullptr) == cudaSuccess ? FFT3D_OK : fail(FFT3D_ERR_CUDA);
     if (!(ns->exec && ns->g_u == uhat && ns->g_ws == ns->workspace && ns->g_nu == nu && ns->g_dt == dt)) {
         drop_ns_graph(ns);
+        cudaStream_t s2 = nl_second_stream(ns->nl);
         if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return fail(FFT3D_ERR_CUDA);
-        const cudaError_t e = enqueue_ns_step(ns, u, nu, dt, s);
+        const cudaError_t e = enqueue_ns_step(ns, u, nu, dt, s, s2);
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(s, &g);
         if (e != cudaSuccess || e2 != cudaSuccess || !g) {
@@ -1541,9 +1639,22 @@ int fft3d_ns_step(fft3d_ns_handle ns, void* uhat, float nu, float dt, void* stre
     return cudaGraphLaunch(ns->exec, s) == cudaSuccess ? FFT3D_OK : fail(FFT3D_ERR_CUDA);
 }
 
+int fft3d_ns_set_chunking(fft3d_ns_handle ns, int planes, int streams)
+{
+    if (!ns) return fail(FFT3D_ERR_INVALID_ARG);
+    const int r = fft3d_nonlinear_set_chunking(ns->nl, planes, streams);
+    if (r == FFT3D_OK) drop_ns_graph(ns);
+    return r;
+}
+
 int fft3d_ns_launches(fft3d_ns_handle ns)
 {
-    return ns ? 2 * 5 + 2 : fail(FFT3D_ERR_INVALID_ARG);
+    if (!ns) return fail(FFT3D_ERR_INVALID_ARG);
+    if (ns->graph) {
+        const int k = graph_kernel_nodes(ns->graph);
+        if (k >= 0) return k;
+    }
+    return 2 * nonlinear_launch_count(ns->nl) + 2;
 }
 
 void fft3d_ns_destroy(fft3d_ns_handle ns)
@@ -1557,7 +1668,29 @@ void fft3d_ns_destroy(fft3d_ns_handle ns)
 
 int fft3d_nonlinear_launches(fft3d_nl_handle nl)
 {
-    return nl ? 5 : fail(FFT3D_ERR_INVALID_ARG);
+    if (!nl) return fail(FFT3D_ERR_INVALID_ARG);
+    if (nl->graph) {
+        const int k = graph_kernel_nodes(nl->graph);
+        if (k >= 0) return k;
+    }
+    return nonlinear_launch_count(nl);
+}
+
+int fft3d_nonlinear_set_chunking(fft3d_nl_handle nl, int planes, int streams)
+{
+    if (!nl || planes < 0 || streams < 1 || streams > 2) return fail(FFT3D_ERR_INVALID_ARG);
+    nl->chunk = planes;
+    nl->streams = streams;
+    drop_graph(nl);  // the next call captures the new order
+    return FFT3D_OK;
+}
+
+int fft3d_nonlinear_get_chunking(fft3d_nl_handle nl, int* planes, int* streams)
+{
+    if (!nl || !planes || !streams) return fail(FFT3D_ERR_INVALID_ARG);
+    *planes = nl->chunk;
+    *streams = nl->streams;
+    return FFT3D_OK;
 }
 
 void fft3d_nonlinear_destroy(fft3d_nl_handle nl)
@@ -1565,6 +1698,9 @@ void fft3d_nonlinear_destroy(fft3d_nl_handle nl)
     if (!nl) return;
     cudaDeviceSynchronize();
     drop_graph(nl);
+    if (nl->s2) cudaStreamDestroy(nl->s2);
+    if (nl->ev_fork) cudaEventDestroy(nl->ev_fork);
+    if (nl->ev_join) cudaEventDestroy(nl->ev_join);
     fft3d_destroy(nl->plan);
     delete nl;
 }

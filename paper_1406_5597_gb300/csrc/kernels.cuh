@@ -207,9 +207,10 @@ __device__ __forceinline__ float2 ld2(const float2* p)
 // the T threads of a row are consecutive lanes.  sm_row: RowLayout<L>::stride
 // float2 of exchange space.
 // Ex: the exchange policy over sm_row (the warp-synchronous padded row by default).
-template <int L, int E, class Ex = RowExchange<true>>
+// TW: the twiddle table (const float2*) or a TwCache of this transform.
+template <int L, int E, class Ex = RowExchange<true>, class TW>
 __device__ __forceinline__ void row_r2c_regs(float2 (&v)[E], float2* out_row, bool active, int t, int lane,
-                                             float2* sm_row, const float2* __restrict__ tw,
+                                             float2* sm_row, const TW& tw,
                                              const float2* __restrict__ twpack, int k2_keep = L + 1)
 {
     constexpr int T = L / E;
@@ -217,7 +218,6 @@ __device__ __forceinline__ void row_r2c_regs(float2 (&v)[E], float2* out_row, bo
     Ex ex{sm_row};
     fft_group<L, E, -1>(v, t, tw, ex);
     const int partner = lane - t + ((T - t) & (T - 1));
-    const float2 wt = __ldg(&twpack[t]);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         float2 g;
@@ -227,7 +227,7 @@ __device__ __forceinline__ void row_r2c_regs(float2 (&v)[E], float2* out_row, bo
         const float2 zc = cconj(t == 0 ? v[(E - m) % E] : g);
         const float2 s = cadd(zk, zc);
         const float2 d = csub(zk, zc);
-        const float2 w = (m == 0) ? wt : cmul(wt, __ldg(&twpack[T * m]));
+        const float2 w = __ldg(&twpack[t + T * m]);  // W^k, k = t + T*m
         const float2 wd = cmul(d, w);  // X = s/2 - (i/2) W^k d
         const int k = t + T * m;
         if (active)
@@ -249,23 +249,27 @@ __device__ __forceinline__ void row_r2c_body(const float2* in_row, float2* out_r
     row_r2c_regs<L, E>(v, out_row, active, t, lane, sm_row, tw, twpack);
 }
 
-// c2r of one row of H bins into registers: v[m] = the real samples 2p, 2p+1
-// at position p = t + T*m (unnormalised).
-// Ex: the exchange policy over sm_row; sm_row may alias in_row (every lane's
-// reads of in_row complete before the first exchange write).
-template <int L, int E, int CG, class Ex = RowExchange<true>>
-__device__ __forceinline__ void row_c2r_regs(const float2* in_row, bool active, int t, int lane, float2* sm_row,
-                                             const float2* __restrict__ tw, const float2* __restrict__ twpack,
-                                             float2 (&v)[E])
+// Loads of one row of H bins for row_c2r_from: x[m] = bin t + T*m, nyq = the
+// Nyquist bin L (thread t = 0 only).  Split from the transform so that a
+// kernel can issue the loads of several rows before the first one's shuffles.
+template <int L, int E, int CG>
+__device__ __forceinline__ void row_c2r_load(const float2* in_row, bool active, int t, float2 (&x)[E], float2& nyq)
+{
+    constexpr int T = L / E;
+#pragma unroll
+    for (int m = 0; m < E; ++m) x[m] = active ? ld2<CG>(&in_row[t + T * m]) : make_float2(0.f, 0.f);
+    nyq = (active && t == 0) ? ld2<CG>(&in_row[L]) : make_float2(0.f, 0.f);
+}
+
+// c2r of one row whose H bins are in registers (row_c2r_load's x, nyq):
+// v[m] = the real samples 2p, 2p+1 at position p = t + T*m (unnormalised).
+template <int L, int E, class Ex = RowExchange<true>, class TW>
+__device__ __forceinline__ void row_c2r_from(const float2 (&x)[E], float2 nyq, int t, int lane, float2* sm_row,
+                                             const TW& tw, const float2* __restrict__ twpack, float2 (&v)[E])
 {
     constexpr int T = L / E;
     static_assert(T <= 32 && (32 % T) == 0, "rows must pack into warps");
-    float2 x[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) x[m] = active ? ld2<CG>(&in_row[t + T * m]) : make_float2(0.f, 0.f);
-    const float2 nyq = (active && t == 0) ? ld2<CG>(&in_row[L]) : make_float2(0.f, 0.f);
     const int partner = lane - t + ((T - t) & (T - 1));
-    const float2 wt = __ldg(&twpack[t]);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         float2 g;
@@ -285,13 +289,27 @@ __device__ __forceinline__ void row_c2r_regs(const float2* in_row, bool active, 
         }
         const float2 s = cadd(xk, xc);
         const float2 d = csub(xk, xc);
-        const float2 w = (m == 0) ? wt : cmul(wt, __ldg(&twpack[T * m]));
+        const float2 w = __ldg(&twpack[t + T * m]);  // W^k, k = t + T*m
         const float2 wd = cmulc(d, w);  // Z = s + i W^{-k} d
         v[m] = make_float2(s.x - wd.y, s.y + wd.x);
     }
     Ex ex{sm_row};
     ex.sync();
     fft_group<L, E, +1>(v, t, tw, ex);
+}
+
+// c2r of one row of H bins into registers: v[m] = the real samples 2p, 2p+1
+// at position p = t + T*m (unnormalised).
+// Ex: the exchange policy over sm_row; sm_row may alias in_row (every lane's
+// reads of in_row complete before the first exchange write).
+template <int L, int E, int CG, class Ex = RowExchange<true>>
+__device__ __forceinline__ void row_c2r_regs(const float2* in_row, bool active, int t, int lane, float2* sm_row,
+                                             const float2* __restrict__ tw, const float2* __restrict__ twpack,
+                                             float2 (&v)[E])
+{
+    float2 x[E], nyq;
+    row_c2r_load<L, E, CG>(in_row, active, t, x, nyq);
+    row_c2r_from<L, E, Ex>(x, nyq, t, lane, sm_row, tw, twpack, v);
 }
 
 // c2r of one row: in_row = H bins, out_row = packed real row (L float2).
@@ -316,8 +334,30 @@ __device__ __forceinline__ void row_c2r_body(const float2* in_row, float2* out_r
 // registers, and each product row transformed back (r2c) with the 2/3 rule on
 // k2 applied.  in: 3 fields of rows x H bins (field stride fs); out: 6 fields.
 
+// The six products of one row set's velocity samples u (registers), each
+// taken back to bins with the k2 part of the 2/3 rule and stored.
+template <int L, int E, class TW>
+__device__ __forceinline__ void nl_products_r2c(const float2 (&u)[3][E], const NlRowArgs& a, long long row,
+                                                bool active, int t, int lane, float2* smr, const TW& tw)
+{
+    constexpr int H = L + 1;
+    constexpr int PI[6] = {0, 0, 0, 1, 1, 2};
+    constexpr int PJ[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        float2 z[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+            z[m] = make_float2(u[PI[q]][m].x * u[PJ[q]][m].x, u[PI[q]][m].y * u[PJ[q]][m].y);
+        row_r2c_regs<L, E>(z, a.out + q * a.fs + row * H, active, t, lane, smr, tw, a.twpack, a.k2_keep);
+    }
+}
+
+// Short rows (E <= 8): 128 registers, so that eight CTAs fit an SM; the
+// kernel is issue-bound, and more resident warps hide the shuffle and
+// exchange latencies.
 template <int L, int E, int ROWS>
-__global__ void __launch_bounds__((L / E) * ROWS) row_nonlinear_kernel(NlRowArgs a)
+__global__ void __launch_bounds__((L / E) * ROWS, E <= 8 ? 8 : 1) row_nonlinear_kernel(NlRowArgs a)
 {
     extern __shared__ float2 sm[];
     constexpr int T = L / E;
@@ -328,18 +368,23 @@ __global__ void __launch_bounds__((L / E) * ROWS) row_nonlinear_kernel(NlRowArgs
     const bool active = row < a.rows;
     float2* smr = sm + r * RowLayout<L>::stride;
     float2 u[3][E];
+    if constexpr (E <= 8) {
+        // the loads of all three rows first, so that three rows' worth of
+        // requests are in flight before the first c2r (few registers per row)
+        float2 x[3][E], nyq[3];
 #pragma unroll
-    for (int f = 0; f < 3; ++f) row_c2r_regs<L, E, false>(a.in + f * a.fs + row * H, active, t, lane, smr, a.tw,
-                                                          a.twpack, u[f]);
-    constexpr int PI[6] = {0, 0, 0, 1, 1, 2};
-    constexpr int PJ[6] = {0, 1, 2, 1, 2, 2};
+        for (int f = 0; f < 3; ++f) row_c2r_load<L, E, false>(a.in + f * a.fs + row * H, active, t, x[f], nyq[f]);
+        // the nine transforms of the thread share their twiddles: formed once
+        TwCache<L, E> twc;
+        twc.fill(a.tw, t);
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        float2 z[E];
+        for (int f = 0; f < 3; ++f) row_c2r_from<L, E>(x[f], nyq[f], t, lane, smr, twc, a.twpack, u[f]);
+        nl_products_r2c<L, E>(u, a, row, active, t, lane, smr, twc);
+    } else {
 #pragma unroll
-        for (int m = 0; m < E; ++m)
-            z[m] = make_float2(u[PI[q]][m].x * u[PJ[q]][m].x, u[PI[q]][m].y * u[PJ[q]][m].y);
-        row_r2c_regs<L, E>(z, a.out + q * a.fs + row * H, active, t, lane, smr, a.tw, a.twpack, a.k2_keep);
+        for (int f = 0; f < 3; ++f)
+            row_c2r_regs<L, E, false>(a.in + f * a.fs + row * H, active, t, lane, smr, a.tw, a.twpack, u[f]);
+        nl_products_r2c<L, E>(u, a, row, active, t, lane, smr, a.tw);
     }
 }
 

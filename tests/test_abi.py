@@ -81,7 +81,12 @@ def test_null_handles(lib):
     assert fft3d.fft3d_ns_step(None, 16, 0.01, 0.1) == fft3d.FFT3D_ERR_INVALID_ARG
     assert fft3d.fft3d_ns_workspace_bytes(None) == 0
     assert fft3d.fft3d_ns_launches(None) == fft3d.FFT3D_ERR_INVALID_ARG
+    assert fft3d.fft3d_ns_set_chunking(None, 8, 2) == fft3d.FFT3D_ERR_INVALID_ARG
     fft3d.fft3d_ns_destroy(None)
+    assert fft3d.fft3d_nonlinear_launches(None) == fft3d.FFT3D_ERR_INVALID_ARG
+    assert fft3d.fft3d_nonlinear_set_chunking(None, 8, 1) == fft3d.FFT3D_ERR_INVALID_ARG
+    with pytest.raises(fft3d.Fft3dError):
+        fft3d.fft3d_nonlinear_get_chunking(None)
     with pytest.raises(fft3d.Fft3dError):
         fft3d.fft3d_get_plane_choice(None)
     buf = ctypes.create_string_buffer(8)

@@ -8,6 +8,8 @@ for the round trip.  The forward result is compared with the oracle's r2c of
 the SAME FP32-rounded input promoted to FP64; the inverse with the oracle's
 c2r of the SAME complex64 input, so the two directions' errors stay apart.
 """
+import functools
+
 import numpy as np
 import pytest
 import torch
@@ -372,8 +374,10 @@ def test_padded_and_preserve_flag_combinations(cuda_lib):
     lib.fft3d_destroy(raw)
 
 
-@pytest.mark.parametrize("shape", [(32, 32, 32), (16, 32, 64), (64, 64, 64)], ids=lambda s: "x".join(map(str, s)))
-def test_navier_stokes_step_matches_oracle(cuda_lib, shape):
+@pytest.mark.parametrize("shape,chunking", [((32, 32, 32), (0, 1)), ((16, 32, 64), (0, 1)), ((64, 64, 64), (0, 1)),
+                                            ((64, 64, 64), (16, 2)), ((16, 32, 64), (3, 1))],
+                         ids=lambda v: "x".join(map(str, v)) if len(v) == 3 else "c%d_s%d" % v)
+def test_navier_stokes_step_matches_oracle(cuda_lib, shape, chunking):
     """One Heun step of the pseudo-spectral Navier-Stokes equations (nonlinear
     term twice, two fused stage kernels, one captured graph) against the FP64
     oracle step: the new state within 1e-6, its increment within 5e-5 (both
@@ -388,7 +392,12 @@ def test_navier_stokes_step_matches_oracle(cuda_lib, shape):
     dt = float(0.01 * np.linalg.norm(U) / np.linalg.norm(r0))  # |increment| about 1 % of |u|
     ref = oracle.ns_step_rk2(U, n2, nu, np.float32(dt))
     ns = lib.NavierStokes(n0, n1, n2)
-    assert lib.fft3d_ns_launches(ns.handle) == 12
+    assert lib.fft3d_ns_set_chunking(ns.handle, *chunking) == lib.FFT3D_OK
+    # two nonlinear terms (n0 inverse; per chunk of planes n1 inverse, rows, n1
+    # forward; the n0 forward over two kept k1 blocks) and two stage kernels
+    chunks = -(-n0 // chunking[0]) if 0 < chunking[0] < n0 else 1
+    launches = 2 * (1 + 3 * chunks + 2) + 2
+    assert lib.fft3d_ns_launches(ns.handle) == launches
     mask = oracle.dealias_mask(n0, n1, n2)
     results = []
     u = torch.from_numpy(U64).cuda()
@@ -403,6 +412,7 @@ def test_navier_stokes_step_matches_oracle(cuda_lib, shape):
             ns.step(u, nu, dt, stream=side)
             side.synchronize()
             results.append(u.cpu().numpy())
+    assert lib.fft3d_ns_launches(ns.handle) == launches  # now the kernel nodes of the captured graph
     for got in results:
         got = got.astype(np.complex128)
         assert rel_l2(got, ref) <= 1e-6
@@ -549,14 +559,29 @@ def test_argument_errors_leave_output_untouched(cuda_lib):
 TOL_NL = 1e-5
 
 
-@pytest.mark.parametrize("shape", [(32, 32, 32), (32, 48, 64), (256, 256, 256), (22, 13, 32)],
-                         ids=lambda s: "x".join(map(str, s)))
-def test_nonlinear_term_matches_oracle(cuda_lib, shape):
+NL_CASES = [((32, 32, 32), (0, 1)), ((32, 48, 64), (0, 1)), ((256, 256, 256), (0, 1)), ((22, 13, 32), (0, 1)),
+            # plane chunks of the middle passes: ragged last chunk, one plane per
+            # chunk, two streams, a chunk larger than n0, the Bluestein axes
+            ((32, 32, 32), (5, 1)), ((32, 48, 64), (1, 2)), ((32, 48, 64), (7, 2)), ((256, 256, 256), (16, 2)),
+            ((256, 256, 256), (48, 1)), ((22, 13, 32), (4, 2)), ((16, 32, 64), (64, 2))]
+
+
+@functools.lru_cache(maxsize=4)
+def _nl_case(shape):
     n0, n1, n2 = shape
-    U = synth.spectral_velocity(n0, n1, n2, seed=synth.seed_for_config(4))
-    U64 = U.astype(np.complex64)
-    ref = oracle.nonlinear_term(U64.astype(np.complex128), n2)
+    U64 = synth.spectral_velocity(n0, n1, n2, seed=synth.seed_for_config(4)).astype(np.complex64)
+    return U64, oracle.nonlinear_term(U64.astype(np.complex128), n2)
+
+
+@pytest.mark.parametrize("shape,chunking", NL_CASES,
+                         ids=lambda v: "x".join(map(str, v)) if len(v) == 3 else "c%d_s%d" % v)
+def test_nonlinear_term_matches_oracle(cuda_lib, shape, chunking):
+    n0, n1, n2 = shape
+    U64, ref = _nl_case(shape)
     nl = cuda_lib.NonlinearTerm(n0, n1, n2)
+    assert cuda_lib.fft3d_nonlinear_set_chunking(nl.handle, *chunking) == cuda_lib.FFT3D_OK
+    assert cuda_lib.fft3d_nonlinear_get_chunking(nl.handle) == chunking
+    planned = cuda_lib.fft3d_nonlinear_launches(nl.handle)
     ud = torch.from_numpy(U64).cuda()
     u_before = ud.clone()
     out = torch.empty((6, n0, n1, n2 // 2 + 1), dtype=torch.complex64, device="cuda")
@@ -570,6 +595,7 @@ def test_nonlinear_term_matches_oracle(cuda_lib, shape):
         nl(ud, out=out, stream=stream)   # same operands: the graph is replayed
         results.append(out.clone())
     stream.synchronize()
+    assert cuda_lib.fft3d_nonlinear_launches(nl.handle) == planned  # the captured graph's kernel nodes
     results.append(nl(ud, stream=False))  # legacy default stream: direct launches
     torch.cuda.synchronize()
     assert torch.equal(ud, u_before)     # the input spectra are preserved
