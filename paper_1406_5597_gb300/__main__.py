@@ -3,10 +3,13 @@ random data on the current CUDA device, through the C ABI.
 
     python -m paper_1406_5597_gb300 --shape 512,512,512 [--flags 0x40] [--dtype f32|bf16x3|f16|f64]
     python -m paper_1406_5597_gb300 --shape 256,256,256 --ns
+    python -m paper_1406_5597_gb300 --shape 256,256,256 --nl
 
 Prints the plan description and the round-trip relative L2 error
 (c2r(r2c(x)) / N against x).  With --ns it instead runs one pseudo-spectral
-Navier-Stokes step (fft3d_ns_step, direct launches) on random spectra.  Useful
+Navier-Stokes step (fft3d_ns_step, direct launches) on random spectra, with
+--nl two applications of the nonlinear term (fft3d_nonlinear_exec, direct
+launches: a warm-up and the one a profiler skips to).  Useful
 as the target of a profiler run: it launches exactly the kernels of one
 transform pair (or one step).
 """
@@ -14,7 +17,7 @@ import argparse
 
 import torch
 
-from . import FFT3D_F32, FFT3D_F32_TC_BF16X3, FFT3D_F32_TC_F16, FFT3D_F64, NavierStokes, Plan, load
+from . import FFT3D_F32, FFT3D_F32_TC_BF16X3, FFT3D_F32_TC_F16, FFT3D_F64, NavierStokes, NonlinearTerm, Plan, load
 
 
 def main() -> None:
@@ -25,6 +28,7 @@ def main() -> None:
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16x3", "f16", "f64"])
     ap.add_argument("--seed", type=int, default=1408)
     ap.add_argument("--ns", action="store_true", help="one Navier-Stokes step instead of r2c + c2r")
+    ap.add_argument("--nl", action="store_true", help="nonlinear-term applications instead of r2c + c2r")
     args = ap.parse_args()
     n0, n1, n2 = (int(v) for v in args.shape.split(","))
     dtype = {"f32": FFT3D_F32, "bf16x3": FFT3D_F32_TC_BF16X3, "f16": FFT3D_F32_TC_F16, "f64": FFT3D_F64}[args.dtype]
@@ -40,6 +44,16 @@ def main() -> None:
         torch.cuda.synchronize(dev)
         print(f"one Navier-Stokes step at {n0}x{n1}x{n2}: |u| = {float(u.abs().norm()):.6e}")
         ns.close()
+        return
+    if args.nl:
+        nl = NonlinearTerm(n0, n1, n2)
+        u = torch.randn((3, n0, n1, n2 // 2 + 1), dtype=torch.complex64, device=dev, generator=gen)
+        out = torch.empty((6, n0, n1, n2 // 2 + 1), dtype=torch.complex64, device=dev)
+        for _ in range(2):
+            nl(u, out=out, stream=False)
+        torch.cuda.synchronize(dev)
+        print(f"nonlinear term at {n0}x{n1}x{n2}: |N| = {float(out.abs().norm()):.6e}")
+        nl.close()
         return
     lead = (args.batch,) if args.batch > 1 else ()
     x = torch.randn(lead + (n0, n1, n2), device=dev, generator=gen, dtype=rt)

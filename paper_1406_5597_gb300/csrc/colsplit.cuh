@@ -393,6 +393,8 @@ struct L2SplitGeom {
     static constexpr int WS = SHIFT ? kSplitW + 2 : kSplitW;                          // slot row width
     static constexpr unsigned SUB_BYTES = (unsigned)kSplitLC * WS * sizeof(float2);  // 64 / 72 KB
     static_assert(!SHIFT || C % 2 == 0, "an odd stride needs an even C for 16-byte row strides");
+    static_assert(kSplitW * sizeof(float2) == 128 && NT % 32 == 0 && 32 % kSplitW == 0,
+                  "a parked row is one 128-byte L2 line, read by the lanes of one warp");
     // PARK: residue C-2 is parked in shared memory next to the ring, the
     // others (0 .. C-3, or 0 .. C-2 without PARK) in L2 scratch
     static constexpr int NL2 = PARK ? C - 2 : C - 1;  // residues parked in L2
@@ -516,6 +518,17 @@ __global__ void __launch_bounds__(L2SplitGeom<C, PARK, SHIFT>::NT) col_l2split_k
                                 cscale(z[mm][q], col_out_factor(kp + LC * q, L, a.scale, a.mask23));
                     }
                 }
+            }
+            // the parked rows just combined are dead: a row (one 128-byte line
+            // of W values) is read by the W lanes of one warp, so once the warp
+            // has them its first lane drops the lines from L2 unwritten (the
+            // next tile parks whole lines again)
+            __syncwarp();
+            if (c == 0) {
+#pragma unroll
+                for (int mm = 0; mm < MB; ++mm)
+#pragma unroll
+                    for (int q = 0; q < NL2; ++q) discard_l2_line(&mine[((size_t)q * LC + T * (m0 + mm)) * W]);
             }
         }
         fence_proxy_async_smem();  // order this thread's shared accesses before the slot's next bulk copy

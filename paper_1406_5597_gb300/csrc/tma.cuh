@@ -74,6 +74,15 @@ __device__ __forceinline__ void bulk_load(void* smem_dst, const void* src, unsig
                  : "memory");
 }
 
+// Invalidate the 128-byte L2 line at p (128-byte aligned) without writing it
+// back: for scratch whose contents are dead once read, so that its dirty lines
+// cost no DRAM write when evicted.  Reads of the line after it see
+// indeterminate values until it is written again.
+__device__ __forceinline__ void discard_l2_line(const void* p)
+{
+    asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(p) : "memory");
+}
+
 // 2D tiled bulk prefetch global -> L2 (no shared memory, no completion).
 __device__ __forceinline__ void tma_prefetch_l2_2d(const CUtensorMap* map, int x, int y)
 {
