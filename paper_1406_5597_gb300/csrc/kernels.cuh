@@ -416,8 +416,18 @@ __global__ void __launch_bounds__((L / E) * ROWS) row_r2c_warp_kernel(RowArgs a)
                               sm + r * RowLayout<L>::stride, a.tw, a.twpack);
 }
 
+// The c2r rows with 32 values per thread (L = 1024) take 147 registers
+// uncapped: 6 CTAs of 64 threads per SM, too few warps to cover the loads of
+// the half-spectrum rows (long-scoreboard stalls); capped at 128, 8 CTAs fit,
+// as for the r2c rows.
 template <int L, int E, int ROWS>
-__global__ void __launch_bounds__((L / E) * ROWS) row_c2r_warp_kernel(RowArgs a)
+constexpr int row_c2r_min_ctas()
+{
+    return (E >= 32 && (L / E) * ROWS <= 64) ? 8 : 1;
+}
+
+template <int L, int E, int ROWS>
+__global__ void __launch_bounds__((L / E) * ROWS, row_c2r_min_ctas<L, E, ROWS>()) row_c2r_warp_kernel(RowArgs a)
 {
     extern __shared__ float2 sm[];
     constexpr int T = L / E;
