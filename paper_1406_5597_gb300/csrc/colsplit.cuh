@@ -389,7 +389,12 @@ struct L2SplitGeom {
     static constexpr int L = kSplitLC * C;
     static constexpr int T = kSplitLC / kSplitE;  // 16 threads per column
     static constexpr int NT = kSplitW * T;         // 256 threads
-    static constexpr int STAGES = 2;
+    // ring depth: at C = 2 (unshifted) three slots, which keep two residues'
+    // copies in flight while the third serves the exchange and the combine
+    // (1024^3 n0 pass 1.95 -> 1.80 ms); measured slower at C = 4 (2048^3
+    // forward 17.05 -> 17.6 ms) and for the shifted maps (up to 1.5x), and
+    // with a residue parked in shared memory only two fit
+    static constexpr int STAGES = (C == 2 && !SHIFT && !PARK) ? 3 : 2;
     static constexpr int WS = SHIFT ? kSplitW + 2 : kSplitW;                          // slot row width
     static constexpr unsigned SUB_BYTES = (unsigned)kSplitLC * WS * sizeof(float2);  // 64 / 72 KB
     static_assert(!SHIFT || C % 2 == 0, "an odd stride needs an even C for 16-byte row strides");
@@ -434,7 +439,7 @@ __global__ void __launch_bounds__(L2SplitGeom<C, PARK, SHIFT>::NT) col_l2split_k
     auto issue = [&](long long n) {
         const long long tile = blockIdx.x + (n / C) * (long long)gridDim.x;
         if (tile >= ntiles) return;
-        const int r = (int)(n % C), s = (int)(n & 1);
+        const int r = (int)(n % C), s = (int)(n % STAGES);
         const long long b = tile / ctiles;
         const long long c0 = (tile - b * ctiles) * W;
         mbar_arrive_expect_tx(&bars[s], G::SUB_BYTES);
@@ -445,20 +450,23 @@ __global__ void __launch_bounds__(L2SplitGeom<C, PARK, SHIFT>::NT) col_l2split_k
         ++n_issued;
     };
 
-    if (leader) issue(0);
+    if (leader) {
+#pragma unroll
+        for (int k = 0; k < STAGES - 1; ++k) issue(k);
+    }
     long long n_consumed = 0;
     bool failed = false;
     for (long long n = 0;; ++n) {
         const long long tile = blockIdx.x + (n / C) * (long long)gridDim.x;
         if (tile >= ntiles) break;
-        const int r = (int)(n % C), s = (int)(n & 1);
-        const bool ok = mbar_wait_bounded(&bars[s], (unsigned)((n >> 1) & 1), kMbarMaxTries);
+        const int r = (int)(n % C), s = (int)(n % STAGES);
+        const bool ok = mbar_wait_bounded(&bars[s], (unsigned)((n / STAGES) & 1), kMbarMaxTries);
         if (!__syncthreads_and(ok)) {
             failed = true;
             break;
         }
         ++n_consumed;
-        if (leader) issue(n + 1);  // into the slot consumed at n - 1
+        if (leader) issue(n + STAGES - 1);  // into the slot consumed at n - 1
         const long long b = tile / ctiles;
         const long long c0 = (tile - b * ctiles) * W;
         const bool active = (c0 + c) < a.C;
@@ -536,7 +544,7 @@ __global__ void __launch_bounds__(L2SplitGeom<C, PARK, SHIFT>::NT) col_l2split_k
     if (failed && leader) {
         atomicOr(a.status, kStatusTimeout);
         for (long long k = n_consumed; k < n_issued; ++k)
-            mbar_wait_bounded(&bars[k & 1], (unsigned)((k >> 1) & 1), kMbarMaxTries);
+            mbar_wait_bounded(&bars[k % STAGES], (unsigned)((k / STAGES) & 1), kMbarMaxTries);
     }
 }
 
