@@ -501,14 +501,41 @@ __global__ void __launch_bounds__(L2SplitGeom<C, PARK, SHIFT>::NT) col_l2split_k
 #pragma unroll
         for (int m = 0; m < E; ++m) buf[(t + T * m) * W + c] = v[m];
         float2* dst = (a.dst ? a.dst : a.data) + b * a.Bs + c0 + c;
+        // The parked values are loaded MB positions at a time.  At C = 2 the
+        // batches are double buffered, the next batch's loads issued before
+        // this batch is combined, so that one L2 round trip is exposed instead
+        // of E/MB (1024^3 n0 pass 1.80 -> 1.77 ms); at C = 4 that spills, and
+        // neither it nor smaller batches were faster there or at C = 3.
         constexpr int MB = 8;
-#pragma unroll
-        for (int m0 = 0; m0 < E; m0 += MB) {
-            float2 z[MB][C];
+        constexpr bool DB = C == 2;
+        float2 zn[DB ? MB : 1][DB ? NL2 : 1];  // DB: the next batch
+        if constexpr (DB) {
 #pragma unroll
             for (int mm = 0; mm < MB; ++mm)
 #pragma unroll
-                for (int q = 0; q < NL2; ++q) z[mm][q] = __ldcg(&mine[((size_t)q * LC + T * (m0 + mm)) * W]);
+                for (int q = 0; q < NL2; ++q) zn[mm][q] = __ldcg(&mine[((size_t)q * LC + T * mm) * W]);
+        }
+#pragma unroll
+        for (int m0 = 0; m0 < E; m0 += MB) {
+            float2 z[MB][C];
+            if constexpr (DB) {
+#pragma unroll
+                for (int mm = 0; mm < MB; ++mm)
+#pragma unroll
+                    for (int q = 0; q < NL2; ++q) z[mm][q] = zn[mm][q];
+                if (m0 + MB < E) {
+#pragma unroll
+                    for (int mm = 0; mm < MB; ++mm)
+#pragma unroll
+                        for (int q = 0; q < NL2; ++q)
+                            zn[mm][q] = __ldcg(&mine[((size_t)q * LC + T * (m0 + MB + mm)) * W]);
+                }
+            } else {
+#pragma unroll
+                for (int mm = 0; mm < MB; ++mm)
+#pragma unroll
+                    for (int q = 0; q < NL2; ++q) z[mm][q] = __ldcg(&mine[((size_t)q * LC + T * (m0 + mm)) * W]);
+            }
 #pragma unroll
             for (int mm = 0; mm < MB; ++mm) {
                 if constexpr (PARK) z[mm][C - 2] = park[(t + T * (m0 + mm)) * W + c];
