@@ -247,9 +247,13 @@ double fft3d_pass_bytes(fft3d_handle plan, int pass);
  * kernel, 2 and 3 the first and second cluster-split kernel compiled for that
  * axis length, 4 the TMA-fed cluster split (lengths 1024, 1536, 2048: 512-row
  * TMA sub-transforms on 2, 3 or 4 CTAs; it needs an even axis stride of at
- * least 16 complex values and otherwise runs as form 0), 5 (n0 pass only)
- * the residue split through L2 (same lengths and condition: one CTA per tile,
- * the 512-row residues parked in plan-owned scratch), where one exists)
+ * least 16 complex values and otherwise runs as form 0), 5 the residue split
+ * through L2 (same lengths: one CTA per tile, the 512-row residues parked in
+ * plan-owned scratch; on an odd axis stride, as the n1 pass with odd n2/2 + 1,
+ * the odd residues read through maps started one value early), 6 (lengths
+ * 1024 and 2048, odd axis stride) the TMA row-pair kernel with two columns
+ * per thread and 16-byte shared and even-row global accesses (on an even
+ * stride it runs as form 1), where one exists)
  * that fft3d_get_choices / fft3d_set_choices
  * read and write (host array), so a caller can cache them per GPU and shape;
  * fft3d_set_choices rejects a form the axis does not have.

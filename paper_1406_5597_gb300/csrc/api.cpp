@@ -668,7 +668,11 @@ cudaError_t launch_col_args(fft3d_plan_s* p, const Axis& a, int dir, const ColAr
         return dir < 0 ? se->fwd(ca, 0, s) : se->inv(ca, 0, s);
     }
     const int mode = tma_mode(p, a, ca.S, ca.C, ca.Bs);
-    if (form == 1 && mode) {
+    if (form == 6 && mode == 2 && a.spec->tma_pair2_fwd) {  // row pairs, two columns per thread
+        CUtensorMap m;
+        if (tensor_map(p, a, ca, true, &m)) return dir < 0 ? a.spec->tma_pair2_fwd(ca, m, s) : a.spec->tma_pair2_inv(ca, m, s);
+    }
+    if ((form == 1 || form == 6) && mode) {
         CUtensorMap m;
         if (tensor_map(p, a, ca, mode == 2, &m)) {
             if (mode == 2) return dir < 0 ? a.spec->tma_pair_fwd(ca, m, s) : a.spec->tma_pair_inv(ca, m, s);
@@ -726,6 +730,10 @@ std::string axis_desc(const fft3d_plan_s* p, const Axis& a, bool row)
                            : a.spec->row_rows;
         std::snprintf(b, sizeof b, "L=%d E=%d rows/CTA=%d %s", a.L, a.spec->row_E, rr,
                       a.spec->row_warp ? "warp" : "smem");
+    } else if (((&a == &p->ax0) ? p->choice_tma : p->choice_tma1) == 6 && a.spec->tma_pair2_fwd &&
+               (&a == &p->ax0 ? tma_mode(p, a, p->P, p->P, p->M) : tma_mode(p, a, p->H, p->H, (long long)p->n1 * p->H)) == 2) {
+        std::snprintf(b, sizeof b, "L=%d E=%d cols/CTA=%d tma-row-pairs 2 cols/thread", a.L, a.spec->tma_pair_E,
+                      a.spec->tma_W);
     } else if (((&a == &p->ax0) ? p->choice_tma : p->choice_tma1) == 5 && a.l2split) {
         std::snprintf(b, sizeof b, "L=%d E=32 cols/CTA=16 tma-residue-split C=%d via L2", a.L, a.l2split->C);
     } else if (((&a == &p->ax0) ? p->choice_tma : p->choice_tma1) == 4 && a.tsplit &&
@@ -1747,10 +1755,11 @@ int fft3d_get_choices(fft3d_handle p, int* c)
 
 int fft3d_set_choices(fft3d_handle p, const int* c)
 {
-    // column forms: 0 plain, 1 TMA ring, 2 + i the axis's i-th cluster-split kernel (must exist)
+    // column forms: 0 plain, 1 TMA ring, 2 + i the axis's i-th cluster-split kernel (must exist),
+    // 4 TMA-fed cluster split, 5 residue split, 6 TMA row pairs with two columns per thread
     auto form_ok = [](int f, const Axis& a) {
         return f == 0 || f == 1 || ((f == 2 || f == 3) && a.split[f - 2]) || (f == 4 && a.tsplit) ||
-               (f == 5 && a.l2split);
+               (f == 5 && a.l2split) || (f == 6 && a.spec && a.spec->tma_pair2_fwd);
     };
     if (!p || !c || c[0] < 0 || c[1] < 0 || c[2] < 0 || !form_ok(c[3], p->ax0) || !form_ok(c[4], p->ax1))
         return fail(FFT3D_ERR_INVALID_ARG);
@@ -1822,8 +1831,11 @@ int fft3d_autotune(fft3d_handle p, float* real, void* cplx, int reps, void* stre
             if (t < best) best = t, pick = w, pick_tma = 0;
         }
         p->choice_w1 = pick;
-        for (int f = 2; f <= 5; ++f) {  // split kernels: cluster (plain, TMA-fed), residues through L2
-            if (f < 4 ? !p->ax1.split[f - 2] : f == 4 ? (!p->ax1.tsplit || H % 2 || H < 16) : !p->ax1.l2split)
+        for (int f = 2; f <= 6; ++f) {  // split kernels: cluster (plain, TMA-fed), residues through L2; 2-column row pairs
+            if (f < 4 ? !p->ax1.split[f - 2]
+                      : f == 4 ? (!p->ax1.tsplit || H % 2 || H < 16)
+                               : f == 5 ? !p->ax1.l2split
+                                        : (!p->ax1.spec->tma_pair2_fwd || tma_mode(p, p->ax1, H, H, n1 * H) != 2))
                 continue;
             p->choice_tma1 = f;
             const float t = time_pass([&] { run_col(p, p->ax1, -1, X, H, H, B * n0, n1 * H, s); }, reps, s);

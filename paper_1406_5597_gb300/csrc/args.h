@@ -127,6 +127,8 @@ struct LenEntry {
     bool row_warp;        // rows resident in warps (shuffle unpack) or staged in shared memory
     RowFn r2c, c2r;
     NlFn nl;              // fused nonlinear-term row kernel (warp rows only)
+    // TMA row pairs with two columns per thread (column form 6; nullptr: none)
+    ColTmaFn tma_pair2_fwd = nullptr, tma_pair2_inv = nullptr;
 };
 
 const LenEntry* find_len(int L);

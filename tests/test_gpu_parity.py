@@ -829,6 +829,41 @@ def test_long_axis_column_forms_match_oracle(cuda_lib, shape):
     plan.close()
 
 
+@pytest.mark.parametrize("shape,batch", [((2, 2048, 32), 1), ((2, 2048, 40), 1), ((3, 1024, 36), 2),
+                                         ((2, 1024, 62), 1), ((4, 1024, 30), 1), ((3, 2048, 4), 1)],
+                         ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else f"b{v}")
+def test_two_column_row_pair_form_matches_oracle(cuda_lib, shape, batch):
+    """Column form 6 of the n1 pass (TMA row pairs, two columns per thread,
+    16-byte exchange and even-row stores) gives the oracle's transform in
+    both directions: odd H (row pairs) with a ragged last tile of one column,
+    batches, and an even H, where the form falls back to the one-column TMA
+    kernel."""
+    lib = cuda_lib
+    n0, n1, n2 = shape
+    H = n2 // 2 + 1
+    lead = (batch,) if batch > 1 else ()
+    x32 = synth.uniform_field(lead + shape, seed=71).astype(np.float32)
+    ref = oracle.r2c3d(x32.astype(np.float64))
+    Y64 = random_half_spectrum((batch * n0, n1, H), 73).reshape(lead + (n0, n1, H))
+    yref = oracle.c2r3d(Y64.astype(np.complex128), n2)
+    plan = lib.Plan(n0, n1, n2, lib.FFT3D_F32, batch, 0)
+    assert lib.fft3d_set_choices(plan.handle, [0, 0, 0, 1, 6]) == lib.FFT3D_OK
+    two = "2 cols/thread" in plan.describe()
+    assert two == (H % 2 == 1 and H >= (4 if n1 == 2048 else 8)), plan.describe()
+    xd = torch.from_numpy(x32).cuda()
+    X = torch.empty(lead + (n0, n1, H), dtype=torch.complex64, device="cuda")
+    plan.r2c(xd.data_ptr(), X.data_ptr())
+    torch.cuda.synchronize()
+    assert rel_l2(X.cpu().numpy(), ref) <= TOL
+    Yd = torch.from_numpy(Y64).cuda()
+    y = torch.empty_like(xd)
+    plan.c2r(Yd.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    assert rel_l2(y.cpu().numpy(), yref) <= TOL
+    assert lib.fft3d_query_device_status(plan.handle) == lib.FFT3D_OK
+    plan.close()
+
+
 @pytest.mark.parametrize("shape,batch", [((2048, 2, 6), 1), ((1024, 3, 10), 1), ((1536, 4, 12), 1),
                                          ((2, 2048, 32), 1), ((3, 1024, 30), 1), ((1024, 2, 8), 2),
                                          ((2048, 3, 4), 2), ((2048, 3, 10), 1), ((1024, 4, 12), 2),
