@@ -978,10 +978,11 @@ fft3d_handle fft3d_plan_variant(int n0, int n1, int n2, int dtype, int batch, in
     // default n0-pass kernel: the plain kernel for long n0 axes, whose rows lie
     // megabytes apart (GB300: n0 = 1024, 16-wide 4.2 TB/s vs TMA 8-wide 2.9;
     // n0 = 1536, 8-wide 2.9 vs 2.5; n0 = 2048, 8-wide 3.0 vs TMA 4-wide 1.3),
-    // and for n0 <= 64 (64^3 x 4 fields: 6.8 vs 7.5 us); the TMA kernel from
-    // 96 to 512 (128^3 x 4: 15.5 vs 18.5 us, 160^3 x 4: 28.7 vs 33.5, 192^3 x
-    // 4: 41 vs 53)
-    if (p->ax0.spec && p->ax0.spec->tma_W && (p->ax0.L <= 64 || p->ax0.L >= 1024)) p->choice_tma = 0;
+    // n0 = 768 (8-wide TMA tiles 1.18 ms vs plain 16-wide 1.07 at 768^3) and
+    // n0 <= 64 (64^3 x 4 fields: 6.8 vs 7.5 us); the TMA kernel from 96 to
+    // 640 (128^3 x 4: 15.5 vs 18.5 us, 192^3 x 4: 41 vs 53, 384^3: 96 vs 122,
+    // 640^3: 0.56 vs 0.69 ms)
+    if (p->ax0.spec && p->ax0.spec->tma_W && (p->ax0.L <= 64 || p->ax0.L >= 768)) p->choice_tma = 0;
     // n0 = 1024, 1536, 2048: the residue split through L2 where it applies
     // (GB300, n0 pass: 1.94 vs 2.05 ms at 1024^3, 6.5-7.3 vs 8.4-8.5 ms at
     // 1536 x 1024 x 2048, 18.9-19.6 vs 22.3-22.5 ms at 2048^3)

@@ -23,6 +23,16 @@ struct ColArgs {
     long long Bs2 = 0;
 };
 
+// Rows per 2D bulk tensor copy of a column tile of `rows` rows: the largest
+// divisor of rows that is at most 256 (the box limit), so that whole boxes
+// tile it (rows <= 256: one box; 512 / 1024: 256; 384: 192; 640: 128).
+__host__ __device__ constexpr int tma_box_rows(int rows)
+{
+    for (int b = rows < 256 ? rows : 256; b > 1; --b)
+        if (rows % b == 0) return b;
+    return 1;
+}
+
 // Output factor of a column pass for output index k of a length-L axis:
 // scale, or 0 where the 2/3 rule drops k (signed k in [-L/2, L/2), so the
 // Nyquist bin is always dropped).

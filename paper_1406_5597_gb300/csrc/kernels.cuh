@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(W*(L / E)) col_tma_kernel(const __grid_constan
     extern __shared__ __align__(1024) unsigned char smraw[];
     constexpr int T = L / E;
     constexpr int ROWS_IN_MAP = PAIR ? L / 2 : L;  // tensor rows per tile (row pairs in PAIR mode)
-    constexpr int BOXR = ROWS_IN_MAP < 256 ? ROWS_IN_MAP : 256;
+    constexpr int BOXR = tma_box_rows(ROWS_IN_MAP);
     constexpr int NBOX = ROWS_IN_MAP / BOXR;
     static_assert(ROWS_IN_MAP % BOXR == 0, "tile rows must split into boxes of <= 256 rows");
     static_assert(!PAIR || (L % 2 == 0 && W % 2 == 0), "row pairs need even L and W");

@@ -32,10 +32,10 @@ cudaError_t col_tensor_map_host(CUtensorMap* map, const ColArgs& a, int L, int W
 {
     if (!pair)
         return encode_tensor_map_2d(map, a.data, 2ull * a.C, (unsigned long long)a.nb * L, 8ull * a.S, 2u * W,
-                                    L < 256 ? L : 256);
+                                    (unsigned)tma_box_rows(L));
     const int rows = L / 2;
     return encode_tensor_map_2d(map, a.data, 4ull * a.S, (unsigned long long)a.nb * rows, 16ull * a.S,
-                                2u * (W + 2), rows < 256 ? rows : 256);
+                                2u * (W + 2), (unsigned)tma_box_rows(rows));
 }
 
 }  // namespace fft3d

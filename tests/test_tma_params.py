@@ -6,7 +6,7 @@ checks it before the copy runs.  The column kernels start tile t at float
 x = 2 * t * W (rows) or, for the odd rows of the row-pair view, at
 2 * (S + t * W - 1) with S odd: both are 16-byte aligned exactly when the tile
 width W is even.  The same instantiations must also split their tile rows into
-boxes of at most 256 rows, keep at least two ring slots (one in flight while
+a few equal boxes of at most 256 rows, keep at least two ring slots (one in flight while
 one is consumed), fit their ring and exchange buffer in 227 KB of shared
 memory, and launch at most 1024 threads.
 """
@@ -62,8 +62,10 @@ def test_tma_boxes_ring_smem_and_threads():
         rows = L // 2 if pair else L
         if pair:
             assert L % 2 == 0, (f, L)
-        box = rows if rows < 256 else 256
-        assert rows % box == 0, (f, L, pair, "tile rows must split into boxes of <= 256 rows")
+        # the kernel's box: the largest divisor of the tile rows that is at most 256
+        box = max(b for b in range(1, min(rows, 256) + 1) if rows % b == 0)
+        assert rows % box == 0 and box <= 256, (f, L, pair, "tile rows must split into boxes of <= 256 rows")
+        assert rows // box <= 8 and (box == rows or box >= 64), (f, L, pair, box, "a few large boxes per tile")
         assert ST >= 2, (f, L, ST)
         ws = W + 2 if pair else W
         smem = ST * L * ws * 8 + (L * W * 8 if _xbuf(L, W, ST, pair) else 0) + 8 * ST
