@@ -237,6 +237,43 @@ def _plan_r2c_c2r(lib, plan, x32, Y64, n2):
     return X.cpu().numpy().astype(np.complex128), y.cpu().numpy().astype(np.float64)
 
 
+# TMA-fed column kernels of the 3*2^k, 5*2^k and short lengths, forced on
+# both axes: n0 tiles (ragged: P not a multiple of the tile width) and n1 row
+# pairs (odd H) or plain rows (even H); boxes of the largest divisor of the
+# tile rows up to 256 for L > 256.
+TMA_LEN_SHAPES = [(64, 3, 12), (2, 64, 32), (96, 5, 12), (2, 96, 32), (128, 3, 10), (2, 128, 34),
+                  (160, 3, 12), (2, 160, 32), (192, 3, 12), (2, 192, 32), (320, 4, 14), (2, 320, 32),
+                  (2, 320, 30), (384, 3, 12), (2, 384, 32), (640, 3, 10), (2, 640, 32), (768, 3, 10),
+                  (2, 768, 32)]
+
+
+@pytest.mark.parametrize("shape", TMA_LEN_SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_tma_column_kernels_of_every_length_match_oracle(cuda_lib, shape):
+    lib = cuda_lib
+    n0, n1, n2 = shape
+    H = n2 // 2 + 1
+    plan = lib.Plan(n0, n1, n2)
+    assert lib.fft3d_set_choices(plan.handle, [0, 0, 0, 1, 1]) == lib.FFT3D_OK
+    desc = plan.describe()
+    long_axis = 0 if n0 > n1 else 1
+    assert ("tma" in desc.split("n0[")[1].split("]")[0]) if long_axis == 0 else \
+        ("tma" in desc.split("n1[")[1].split("]")[0]), desc
+    x32 = synth.uniform_field(shape, seed=79).astype(np.float32)
+    xd = torch.from_numpy(x32).cuda()
+    X = torch.empty((n0, n1, H), dtype=torch.complex64, device="cuda")
+    plan.r2c(xd.data_ptr(), X.data_ptr())
+    torch.cuda.synchronize()
+    assert rel_l2(X.cpu().numpy(), oracle.r2c3d(x32.astype(np.float64))) <= TOL
+    Y = random_half_spectrum((n0, n1, H), seed=83)
+    Yd = torch.from_numpy(Y).cuda()
+    y = torch.empty_like(xd)
+    plan.c2r(Yd.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    assert rel_l2(y.cpu().numpy(), oracle.c2r3d(Y.astype(np.complex128), n2)) <= TOL
+    assert lib.fft3d_query_device_status(plan.handle) == lib.FFT3D_OK
+    plan.close()
+
+
 @pytest.mark.parametrize("shape", [(9, 32, 32), (10, 64, 64), (5, 128, 128), (6, 256, 256), (3, 512, 512),
                                    (4, 96, 96), (3, 160, 160), (2, 192, 192)],
                          ids=lambda s: "x".join(map(str, s)))
