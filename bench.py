@@ -21,6 +21,8 @@ with its own roofline:
   relative L2 errors against the FP64 oracle in both directions (the field is
   the oracle's c2r of the spectrum S, computed on the host cores; that inverse
   and a forward oracle transform of it are the cpu_baseline sample);
+* ``size_1536x1024x2048``: the non-cubic case of the 2048^3 configuration
+  (radix 3 on n0), FP32, autotuned;
 * ``size_512``: 512^3 FP32 with the comparator and layout variants (explicit
   transpose with and without the transpose back, fused and cluster plane
   forms, FFTW's padded in-place layout, input-preserving inverse, FP64) and
@@ -51,6 +53,7 @@ FALLBACK_HBM_GBS = 6800.0
 SEED_2048 = 1411  # 1406 + configuration number
 SEED_1024 = 1409
 SEED_512 = 1408
+SEED_1536 = 1511  # the second field of the 2048^3 configuration (+100)
 # the oracle's sample for the reference arm: a cube whose full step takes a
 # few seconds on the host cores (the 2048^3 step needs 137 GB of FP64 memory)
 REF_SAMPLE_MAX = 512
@@ -657,6 +660,32 @@ def size_1024(ctx, n=1024):
     return rec, cpu
 
 
+def size_1536(ctx, shape=(1536, 1024, 2048)):
+    """1536 x 1024 x 2048 sub-record (the non-cubic case beside the 2048^3
+    field, radix 3 on n0): the spectrum-shaped field drawn on the device,
+    x = its FP32 c2r (set-up), the autotuned FP32 step timed as the others."""
+    import torch
+
+    from synth import device as synth_device
+    n0, n1, n2 = shape
+    H = n2 // 2 + 1
+    Sd = synth_device.spectral_velocity(n0, n1, n2, seed=SEED_1536, device=ctx.dev)
+    x = torch.empty(shape, dtype=torch.float32, device=ctx.dev)
+    X = torch.empty((n0, n1, H), dtype=torch.complex64, device=ctx.dev)
+    y = torch.empty_like(x)
+    setup = ctx.fft3d.Plan(n0, n1, n2)
+    X.copy_(Sd)
+    setup.c2r(X.data_ptr(), x.data_ptr(), ctx.sptr)  # the real field (set-up)
+    setup.close()
+    del Sd
+    plan, rec = measure_size(ctx, shape, x, X, y, autotune=not ctx.args.no_autotune)
+    rec["field"] = f"spectrum-shaped (seed {SEED_1536}); x = the FP32 c2r of S on the GPU"
+    plan.close()
+    del plan, x, X, y
+    torch.cuda.empty_cache()
+    return rec
+
+
 def size_512(ctx, n=512):
     import numpy as np
     import torch
@@ -878,6 +907,8 @@ def main():
             line["size_1024"], cpu = size_1024(ctx)
         if args.shape != (512, 512, 512):
             line["size_512"] = size_512(ctx)
+        if args.shape == (2048, 2048, 2048):
+            line["size_1536x1024x2048"] = size_1536(ctx)
     if not args.no_extras:
         line.update(pseudo_spectral(ctx))
 
