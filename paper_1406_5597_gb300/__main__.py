@@ -4,6 +4,7 @@ random data on the current CUDA device, through the C ABI.
     python -m paper_1406_5597_gb300 --shape 512,512,512 [--flags 0x40] [--dtype f32|bf16x3|f16|f64]
     python -m paper_1406_5597_gb300 --shape 256,256,256 --ns
     python -m paper_1406_5597_gb300 --shape 256,256,256 --nl
+    python -m paper_1406_5597_gb300 --shape 64,1024,2048 --forms 1,6
 
 Prints the plan description and the round-trip relative L2 error
 (c2r(r2c(x)) / N against x).  With --ns it instead runs one pseudo-spectral
@@ -29,6 +30,7 @@ def main() -> None:
     ap.add_argument("--seed", type=int, default=1408)
     ap.add_argument("--ns", action="store_true", help="one Navier-Stokes step instead of r2c + c2r")
     ap.add_argument("--nl", action="store_true", help="nonlinear-term applications instead of r2c + c2r")
+    ap.add_argument("--forms", default=None, help="column forms f0,f1 of the n0 and n1 passes (fft3d_set_choices)")
     args = ap.parse_args()
     n0, n1, n2 = (int(v) for v in args.shape.split(","))
     dtype = {"f32": FFT3D_F32, "bf16x3": FFT3D_F32_TC_BF16X3, "f16": FFT3D_F32_TC_F16, "f64": FFT3D_F64}[args.dtype]
@@ -60,6 +62,12 @@ def main() -> None:
     X = torch.empty(lead + (n0, n1, n2 // 2 + 1), dtype=ct, device=dev)
     y = torch.empty_like(x)
     plan = Plan(n0, n1, n2, dtype, args.batch, args.flags)
+    if args.forms:
+        from . import fft3d_get_choices, fft3d_set_choices
+        ch = fft3d_get_choices(plan.handle)
+        ch[3], ch[4] = (int(v) for v in args.forms.split(","))
+        if fft3d_set_choices(plan.handle, ch) != 0:
+            raise SystemExit(f"forms {args.forms}: not available for this plan")
     s = torch.cuda.current_stream(dev).cuda_stream
     plan.r2c(x.data_ptr(), X.data_ptr(), s)
     plan.c2r(X.data_ptr(), y.data_ptr(), s)
