@@ -603,7 +603,7 @@ NL_CASES = [((32, 32, 32), (0, 1)), ((32, 48, 64), (0, 1)), ((256, 256, 256), (0
             ((256, 256, 256), (48, 1)), ((22, 13, 32), (4, 2)), ((16, 32, 64), (64, 2))]
 
 
-@functools.lru_cache(maxsize=4)
+@functools.lru_cache(maxsize=None)  # one oracle term per distinct shape of NL_CASES
 def _nl_case(shape):
     n0, n1, n2 = shape
     U64 = synth.spectral_velocity(n0, n1, n2, seed=synth.seed_for_config(4)).astype(np.complex64)
